@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Benchmark of the PT-TEBD time step on GB300 (site-steps/s), one JSON line on stdout.
+
+Workload (default): the five-site XYZ chain between a hot (T=5) and a cold (T=0.5) Ohmic bath,
+alpha=0.16, w_c=4, dt=0.05, PT-MPO bond <= 32, chi <= 64, eps = 1e-8 (200-step trajectory).
+A "step" is one full PT-TEBD time step of every chain (three bond layers, the PT site layer,
+three bond layers, readout). W warm-up steps run from t = 0, then K steps are timed, each with
+CUDA events on the library's stream and an L2 flush (a 256 MiB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32x3|bf16x3]
+  python bench.py --impl reference ...     # the FP64 CPU oracle on the host cores, same metric
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PT-TEBD site-steps/s and TFLOP/s vs roofline, FP32-TC vs FP64 at <=1e-5 obs err"
+UNIT = "site-steps/s"
+DEFAULT_WORKLOAD = "xyz5_twobaths"
+SM_COUNT = 152
+FP64_FLOPS_PER_CLK_PER_SM = 4.0       # 2 DFMA / clk / SM: 1.25 TFLOP/s nominal at 2.07 GHz x 152 SMs
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons, sampled every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except Exception:
+            return None
+    return None
+
+
+# ------------------------------------------------------------------------ algorithmic flops
+def bond_sizes(chis, kaps, N):
+    """(m_L, n_L, m_R, n_R, r_L, r_R, chi) of every bond for the given dims (App. A.2)."""
+    out = []
+    for b in range(N - 1):
+        chl, chc, chr_ = chis[b], chis[b + 1], chis[b + 2]
+        mL, nL = chl * kaps[b], 4 * chc
+        mR, nR = 4 * chc, kaps[b + 1] * chr_
+        out.append((mL, nL, mR, nR, min(mL, nL), min(mR, nR), chc))
+    return out
+
+
+def svd_flops(m, n):
+    """Golub-Van Loan dense SVD count with U and V, 4m^2n + 8mn^2 + 9n^3, x4 for complex."""
+    if m < n:
+        m, n = n, m
+    return 4.0 * (4 * m * m * n + 8 * m * n * n + 9 * n ** 3)
+
+
+def step_flops(chis, kaps, N):
+    """Algorithmic flops of one step: 3 bond updates per bond (the O layers twice, E once, per
+    half step -> odd bonds 4x, even bonds 2x), each QR + theta + SVD + recovery, plus the PT layer."""
+    svd = other = 0.0
+    for b, (mL, nL, mR, nR, rL, rR, chc) in enumerate(bond_sizes(chis, kaps, N)):
+        reps = 4 if b % 2 == 0 else 2
+        mD, nD = 4 * rL, 4 * rR
+        f_svd = svd_flops(mD, nD)
+        f_qr = (16.0 * (mL * nL * nL - nL ** 3 / 3) if mL > nL else 0.0) + \
+               (16.0 * (nR * mR * mR - mR ** 3 / 3) if nR > mR else 0.0)
+        f_theta = 128.0 * rL * rR * chc + 2048.0 * rL * rR
+        f_rec = 8.0 * (mL * rL * 4 * chc if mL > nL else 0) + 8.0 * (nR * rR * 4 * chc if nR > mR else 0)
+        svd += reps * f_svd
+        other += reps * (f_qr + f_theta + f_rec)
+    return svd, other
+
+
+# ------------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2201_05529_gb300 as pkg
+    from paper_2201_05529_gb300 import problem as pp
+    from workloads import workload
+
+    torch.cuda.set_device(local)
+    pkg.build()
+    capi = pkg.load()
+    capi.use_torch_allocator(local)
+    w = workload(args.workload)
+    chains, mpos = pp.build_problem(w)
+    K, W = args.steps, args.warmup
+    if W + K > w.K:
+        raise SystemExit(f"warmup + steps must be <= {w.K} (the PT-MPO length of {w.name})")
+    Z = pp.pauli("z")
+    site_steps_per_step = sum(c["N"] for c in chains)
+    n_chains = len(chains)
+
+    def make():
+        e = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, precision=args.precision,
+                        max_steps=w.K, use_graph=True)
+        e.set_observables([Z])
+        return e
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    # --- main timed run: graph replay, per-step events, L2 flush between steps
+    eng = make()
+    eng.step(W)
+    eng.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    dims = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(K):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            eng.step(1)
+            ev[i][1].record(stream)
+            dims.append([eng.get_dims(c) for c in range(n_chains)])   # synchronises; outside the events
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    eng.sync()
+    value = site_steps_per_step * K * world / (total_ms / 1e3)
+
+    # algorithmic flops over the timed steps (bond sizes from the dims at the end of each step)
+    fl_svd = fl_other = 0.0
+    for per_chain in dims:
+        for c, (chi, kap) in enumerate(per_chain):
+            s, o = step_flops(list(chi), list(kap), chains[c]["N"])
+            fl_svd += s
+            fl_other += o
+    eng.destroy()
+
+    # --- per-stage timing (eager launches with events) over the same window
+    eng = make()
+    eng.step(W)
+    eng.sync()
+    eng.set_timing(True)
+    stage = np.zeros(7)
+    nk = min(K, 5)
+    for i in range(nk):
+        flush.fill_(float(i))
+        eng.step(1)
+        stage += eng.get_timing()
+    eng.set_timing(False)
+    eng.destroy()
+    stage /= nk
+    n_layers = 6
+    jac_launch_ms = stage[3] / n_layers
+    steps_svd_flops = fl_svd / K
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    fp64_peak = SM_COUNT * FP64_FLOPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+    achieved = (steps_svd_flops / n_layers) / (jac_launch_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_jacobi (FP64 one-sided Jacobi SVD)",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "traffic": None, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x median SM clock",
+                "stage_ms_per_step": {"site": stage[0], "blocks_qr": stage[1], "theta": stage[2],
+                                      "svd": stage[3], "truncate": stage[4], "recover": stage[5],
+                                      "readout": stage[6]}}
+
+    # --- end to end through the C ABI: host inputs -> init (H2D) -> K steps -> history (D2H)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2 = make()
+    e2.step(K)
+    hist, tr = e2.read_history(0, K + 1)
+    t1 = time.perf_counter()
+    e2.destroy()
+    h2d = 0
+    for c in chains:
+        h2d += c["rho0"].nbytes if c.get("rho0") is not None else 0
+        h2d += (c["gates_q"].nbytes + c["gates_h"].nbytes) if c["N"] > 1 else 0
+    h2d += sum(P.nbytes for Ps in mpos for P in Ps[:K])
+    d2h = hist.nbytes + tr.nbytes
+    e2e = {"value": site_steps_per_step * K / (t1 - t0), "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d / K), "d2h_bytes_per_step": int(d2h / K)}
+    gpu_launches = K * (6 * 6 + (2 if any(any(i >= 0 for i in c["ptmpo_id"]) for c in chains) else 0) + 2)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+           "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+           "data": "synthetic (seeded workload; PT-MPOs built on the host from the stated Ohmic baths)",
+           "config": {"workload": w.name, "chains": n_chains, "N": [c["N"] for c in chains],
+                      "dt": w.dt, "chi_max": w.chi_max, "kappa_max": w.kappa_max, "eps": w.eps,
+                      "precision": args.precision, "window": f"steps {W}..{W + K} of {w.K}",
+                      "l2": "flushed between timed steps (256 MiB write)",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "clocks": clocks, "roofline": roofline, "e2e": e2e, "gpu_launches": gpu_launches,
+           "algorithmic_tflops": (fl_svd + fl_other) / (total_ms / 1e3) / 1e12}
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w, W, args.cpu_seconds, site_steps_per_step)
+    if world > 1:
+        dist.destroy_process_group()
+    return out
+
+
+# ------------------------------------------------------------------------ the oracle on the host
+def cpu_baseline(w, warm, seconds, site_steps_per_step):
+    """Time the FP64 oracle as it stands on the host cores: W untimed steps from t = 0, then as
+    many steps as fit in about `seconds` (at least one)."""
+    from oracle import problem as oprob, model, pttebd
+    cis = oprob.build_inputs(w)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    total_steps = 0
+    t_total = 0.0
+    for ci in cis:
+        m = pttebd.product_state(ci.rho0) if ci.init_mps is None else ci.init_mps.copy()
+        for k in range(1, warm + 1):
+            pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
+        t0 = time.perf_counter()
+        k = warm
+        while k < w.K:
+            k += 1
+            pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
+            total_steps += 1
+            if time.perf_counter() - t0 > seconds / max(1, len(cis)):
+                break
+        t_total += time.perf_counter() - t0
+        if len(cis) > 4 and t_total > seconds:
+            break
+    n_sites_done = total_steps * (site_steps_per_step / len(cis))
+    return {"value": n_sites_done / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{total_steps} steps after {warm} warm-up steps of {w.name} "
+                      f"(numpy/LAPACK, {cores} host threads available)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from workloads import workload
+    w = workload(args.workload)
+    W, K = args.warmup, args.steps
+    from oracle import problem as oprob, pttebd
+    cis = oprob.build_inputs(w)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    site_steps = sum(ci.N for ci in cis)
+    # each "step" of the reference arm is one PT-TEBD step of the same trajectory (bounded: K steps)
+    ms = []
+    states = []
+    for ci in cis:
+        m = pttebd.product_state(ci.rho0) if ci.init_mps is None else ci.init_mps.copy()
+        for k in range(1, W + 1):
+            pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
+        states.append(m)
+    t0 = time.perf_counter()
+    for i in range(K):
+        ts = time.perf_counter()
+        for ci, m in zip(cis, states):
+            pttebd.pt_step(m, W + i + 1, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
+        ms.append((time.perf_counter() - ts) * 1e3)
+    t_all = time.perf_counter() - t0
+    value = site_steps * K / t_all
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": t_all * 1e3 / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "impl": "reference",
+            "data": "synthetic (seeded workload; PT-MPOs built by the oracle)",
+            "config": {"workload": w.name, "chains": len(cis), "precision": "fp64 (numpy/LAPACK)",
+                       "window": f"steps {W}..{W + K} of {w.K}"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{K} steps after {W} warm-up steps of {w.name}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * pt_tebd.h -- C ABI of the GB300 PT-TEBD time step.
+ *
+ * PT-TEBD (arXiv:2201.05529) evolves chains of open quantum systems in Liouville space: an
+ * augmented MPS in Vidal form, Gamma_n[chi_{n-1}][d^2][kappa_n][chi_n] and lambda_n[chi_n]
+ * (App. A.1), is advanced per time step by the second-order splitting of Eq. (propagator-env):
+ * a chain half step, the PT-MPO site contractions (App. A.2, (i-j)), and another chain half step,
+ * each chain half being O(dt/4) E(dt/2) O(dt/4) layers of two-site Liouville gates applied by
+ * the contraction/decomposition sequence (c-h) of App. A.2 with exact QR reductions and an FP64
+ * one-sided Jacobi SVD truncated by the relative rule of App. A.2. Observables are read out by
+ * closing the augmented legs with cap tensors (App. A.3) and the Liouville legs with trace or
+ * observable vectors; two-time correlations insert a left/right super-operator (App. A.4).
+ *
+ * Conventions: spin-1/2, d^2 = 4; basis index 0 = up; row-major vectorisation
+ * vec(rho)[i*2 + j] = rho[i][j]; Tr(O rho) = vec(O^T) . vec(rho). Complex numbers are stored
+ * interleaved (re, im) as doubles. Two-site gates are 16x16 row-major with per-site grouping
+ * [(p'_n*4 + p'_{n+1})][(p_n*4 + p_{n+1})].
+ *
+ * Ownership: every pointer an entry point takes is caller-owned host memory that is copied before
+ * the call returns, except `cuda_stream` (borrowed for the handle's lifetime). The library owns
+ * all device memory of a handle; it comes from the allocator registered with
+ * pt_tebd_set_allocator (e.g. PyTorch's caching allocator), else from cudaMalloc.
+ *
+ * Errors: every int-returning call returns 0 on success or a negative PT_ERR_* code; the message
+ * of the last failure is available from pt_tebd_last_error(). Device-side failures (capacity
+ * overflow, SVD non-convergence, NaN) are recorded in a device status word that is read back at
+ * every synchronising call (pt_tebd_observe, pt_tebd_read_history, pt_tebd_sync).
+ */
+#ifndef PT_TEBD_H
+#define PT_TEBD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PT_OK 0
+#define PT_ERR_ARG (-1)
+#define PT_ERR_OOM (-2)
+#define PT_ERR_CAPACITY (-3)
+#define PT_ERR_SVD_NOCONV (-4)
+#define PT_ERR_DEVICE_TIMEOUT (-5)
+#define PT_ERR_NAN (-6)
+#define PT_ERR_CUDA (-7)
+#define PT_ERR_STEPS (-8)
+
+typedef struct pt_tebd* pt_tebd_t;
+
+typedef enum {
+  PT_FP64 = 0,      /* every stage in FP64 */
+  PT_TF32X3 = 1,    /* contractions in split TF32 on tensor cores, FP32 accumulate; FP64 SVD */
+  PT_BF16X3 = 2,    /* contractions in split BF16 on tensor cores, FP32 accumulate; FP64 SVD */
+  PT_TF32X1 = 3     /* single TF32 products (speed reference only) */
+} pt_precision;
+
+/* One chain (App. A.1). Sites without a bath have ptmpo_id = -1 (augmented leg of dimension 1).
+ * rho0 gives a product initial state; alternatively gamma0/lambda0 give a full augmented MPS
+ * (correlated initial chain-environment state, App. A.1): then rho0 may be NULL. */
+typedef struct {
+  int N;                          /* number of sites, >= 1 */
+  const double* rho0;             /* [N][4] complex: vec(rho_n); ignored if gamma0 != NULL */
+  const double* gates_q;          /* [N-1][16][16] complex: exp(L^{K'}_b dt/4) */
+  const double* gates_h;          /* [N-1][16][16] complex: exp(L^{K'}_b dt/2) */
+  const double* local_prop;       /* [N][4][4] complex on-site propagator applied after the PT
+                                     tensor at each step, or NULL for none */
+  const int* ptmpo_id;            /* [N]: index into pt_mpos, or -1 */
+  const int* chi0;                /* [N+1] initial bond dims (chi0[0] = chi0[N] = 1) or NULL */
+  const int* kappa0;              /* [N] initial augmented dims or NULL */
+  const double* const* gamma0;    /* [N] pointers to Gamma_n[chi0[n]][4][kappa0[n]][chi0[n+1]] complex */
+  const double* const* lambda0;   /* [N+1] pointers to real lambda_n[chi0[n]] */
+} pt_chain_desc;
+
+/* One PT-MPO (App. A.1; shared by every site whose bath is identical). */
+typedef struct {
+  int K;                          /* number of time steps it covers */
+  const int* kappa;               /* [K+1] bond dims; kappa[0] must match the site's initial kappa */
+  const double* const* P;         /* [K] pointers: P^(k+1)[kappa[k]][4][4][kappa[k+1]] complex,
+                                     index [a][p_in][p_out][b] */
+} pt_mpo_desc;
+
+typedef struct {
+  int chi_max;                    /* bond dimension cap */
+  double eps;                     /* relative singular value threshold (App. A.2) */
+  double multiplet_tol;           /* relative gap below which a cut may not split a multiplet */
+  pt_precision precision;
+  int max_steps;                  /* history capacity when no PT-MPO bounds the run (0: 1024) */
+  int max_sweeps;                 /* Jacobi sweep cap before PT_ERR_SVD_NOCONV (0: 60) */
+  int use_graph;                  /* capture one step as a CUDA graph and replay it */
+} pt_options;
+
+/* Device memory hook: alloc(bytes, ctx) returns device memory or NULL; free(ptr, ctx). */
+typedef void* (*pt_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*pt_free_fn)(void* ptr, void* ctx);
+void pt_tebd_set_allocator(pt_alloc_fn alloc, pt_free_fn free_fn, void* ctx);
+
+/* Build a handle: copies the chains, gates and PT-MPOs to the device, builds the caps (App. A.3)
+ * on the device, and prepares the step. cuda_stream is a cudaStream_t (NULL: default stream). */
+int pt_tebd_init(pt_tebd_t* out, const pt_chain_desc* chains, int n_chains,
+                 const pt_mpo_desc* pt_mpos, int n_mpos, const pt_options* opt, void* cuda_stream);
+
+/* Register the single-site operators (row-major 2x2 complex, [n_ops][2][2]) whose expectation
+ * values Tr(O_n rho) are recorded on every site after every step (and now, at the current step). */
+int pt_tebd_set_observables(pt_tebd_t h, const double* ops, int n_ops);
+
+/* Advance every chain by n_steps full steps (asynchronous on the handle's stream). */
+int pt_tebd_step(pt_tebd_t h, int n_steps);
+
+/* Expectation values of ops at the current step, synchronously.
+ * out: [n_chains][N_max][n_ops] complex (host), raw Tr(O rho) or divided by Tr(rho) if normalize;
+ * trace_out: [n_chains] complex (host) or NULL. */
+int pt_tebd_observe(pt_tebd_t h, const double* ops, int n_ops, double* out, double* trace_out,
+                    int normalize);
+
+/* Recorded values of the registered ops for steps [first, first+count):
+ * out [count][n_chains][N_max][n_ops] complex, trace_out [count][n_chains] complex (either NULL). */
+int pt_tebd_read_history(pt_tebd_t h, int first, int count, double* out, double* trace_out);
+
+/* Insert rho -> A rho (side 0) or rho -> rho A (side 1) on one site (App. A.4). */
+int pt_tebd_apply_local(pt_tebd_t h, int chain, int site, const double* op2x2, int side);
+
+/* State queries (synchronous): number of completed steps; bond dims [N+1] and augmented dims [N]
+ * of one chain; lambda of one bond (up to cap doubles); log of the state's norm factor. */
+int pt_tebd_steps_done(pt_tebd_t h);
+int pt_tebd_get_dims(pt_tebd_t h, int chain, int* chi, int* kappa);
+int pt_tebd_get_lambda(pt_tebd_t h, int chain, int bond, double* out, int cap);
+int pt_tebd_get_lognorm(pt_tebd_t h, int chain, double* out);
+
+/* Copy the whole device state into a new handle (App. B.2: continue from the full augmented MPS). */
+int pt_tebd_clone(pt_tebd_t h, pt_tebd_t* out);
+
+/* Wait for the stream and check the device status word. */
+int pt_tebd_sync(pt_tebd_t h);
+
+int pt_tebd_destroy(pt_tebd_t h);
+const char* pt_tebd_last_error(pt_tebd_t h);   /* h may be NULL: last global error */
+
+/* Per-stage device time of the last pt_tebd_step call with timing enabled, in milliseconds:
+ * [0] site contraction, [1] block build + QR, [2] theta + gate, [3] SVD, [4] truncation,
+ * [5] Gamma recovery, [6] readout. */
+int pt_tebd_set_timing(pt_tebd_t h, int enable);
+int pt_tebd_get_timing(pt_tebd_t h, double* ms7);
+
+/* ---- kernel-level entry points (single operations on device buffers, for unit tests) ---- */
+
+/* Batched FP64 SVD (the one-sided Jacobi of the bond update, App. A.2 (f-g)) of `batch` complex
+ * matrices A_b [m][n] row-major (device). Writes singular values sigma [batch][min(m,n)]
+ * (descending), U [batch][m][min(m,n)] and V [batch][n][min(m,n)] (device, row-major), so
+ * A_b = U diag(sigma) V^H. scratch: device workspace of pt_svd_scratch_bytes(m, n, batch) bytes.
+ * Returns PT_ERR_SVD_NOCONV if a matrix did not converge within max_sweeps. */
+size_t pt_svd_scratch_bytes(int m, int n, int batch);
+int pt_svd_f64(const double* A, int m, int n, int batch, double* sigma, double* U, double* V,
+               void* scratch, int max_sweeps, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT_TEBD_H */

@@ -64,7 +64,7 @@ def pt_mpo_cached(bath, dt, K, eps_tempo, kappa_max, n_memory=0):
     try:
         os.makedirs(CACHE_DIR, exist_ok=True)
         tmp = path + f".tmp{os.getpid()}.npz"
-        np.savez(tmp, **{f"P{k}": P[k] for k in range(K)})
+        np.savez_compressed(tmp, **{f"P{k}": P[k] for k in range(K)})
         os.replace(tmp, path)
     except OSError:
         pass

@@ -1,0 +1,98 @@
+// Shared device-side definitions of the PT-TEBD engine (tables, work items, complex helpers).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PT_DEV __device__ __forceinline__
+
+// ---------------------------------------------------------------- complex arithmetic (FP64)
+PT_DEV double2 cmk(double r, double i) { return make_double2(r, i); }
+PT_DEV double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+PT_DEV double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+PT_DEV double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+PT_DEV double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+PT_DEV double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// acc += a * b
+PT_DEV double2 cfma(double2 a, double2 b, double2 acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+// acc += conj(a) * b
+PT_DEV double2 cfma_conj(double2 a, double2 b, double2 acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+PT_DEV double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// ---------------------------------------------------------------- device status word codes
+enum : int {
+  ST_OK = 0,
+  ST_CAPACITY = 1,
+  ST_SVD_NOCONV = 2,
+  ST_NAN = 4,
+  ST_PT_RANGE = 8,
+};
+
+// ---------------------------------------------------------------- engine tables (device)
+// Global site index s, global bond (lambda) index B. Chain c owns sites
+// [site0[c], site0[c] + N[c]) and lambdas [lam0[c], lam0[c] + N[c] + 1).
+struct Tables {
+  double2** site_gam;      // [n_sites] current Gamma buffer, layout [chi_l][4][kappa][chi_r]
+  double2** site_alt;      // [n_sites] second buffer (PT contraction writes here, then swap)
+  int* site_kappa;         // [n_sites] live kappa
+  int* site_mpo;           // [n_sites] PT-MPO index or -1
+  size_t* site_cap;        // [n_sites] capacity of each Gamma buffer (complex elements)
+  double** lam_ptr;        // [n_lams] lambda buffers
+  int* lam_chi;            // [n_lams] live chi
+  int* lam_cap;            // [n_lams] capacity
+  double* lam_lognorm;     // [n_lams] accumulated log of the norms removed at that bond
+  int* chain_site0;
+  int* chain_lam0;
+  int* chain_N;
+  // PT-MPOs (local propagators already fused)
+  int* mpo_K;              // [n_mpos]
+  int* mpo_kappa_off;      // [n_mpos] offset into mpo_kappa (K+1 entries each)
+  int* mpo_kappa;
+  int* mpo_P_off;          // [n_mpos] offset into mpo_P (K pointers each)
+  const double2** mpo_P;   // P^(k+1)[kappa_k][4][4][kappa_{k+1}]
+  int* mpo_cap_off;        // [n_mpos] offset into mpo_cap (K+1 pointers each)
+  double2** mpo_cap;       // C^(k)[kappa_k]
+  int* step;               // [1] completed steps
+  int* status;             // [1] device status word (ST_* bits)
+};
+
+// One two-site bond update (App. A.2 (c-h)) with its private scratch.
+struct BondWork {
+  int chain;
+  int site_l;              // global index of the left site
+  int lam_l;               // global lambda index of the bond left of site_l
+  int pad;
+  const double2* gate;     // 16x16 row-major
+  double2* QL;             // [mL_cap * nL_cap]  B_L (col-major) -> Q_L
+  double2* RL;             // [nL_cap * nL_cap]  R_L (col-major, upper triangle)
+  double2* QR;             // [nR_cap * mR_cap]  B_R^H (col-major) -> Q_R^H
+  double2* LR;             // [mR_cap * mR_cap]  R of B_R^H (col-major)
+  double2* HH;             // Householder vectors, max(mL*nL, nR*mR)
+  double2* A;              // [mD_cap * nD_cap]  D (or D^H) col-major, becomes U (or V)
+  double2* V;              // [k_cap * k_cap]    right factor of the one-sided Jacobi
+  double* sig;             // [k_cap] singular values (unsorted)
+  double* aux;             // [k_cap] column norms scratch
+  int* perm;               // [k_cap] perm[rank] = column
+  int* info;               // [4] per-item: 0 mD, 1 nD, 2 transposed, 3 sweeps
+  int mL_cap, nL_cap, mR_cap, nR_cap, mD_cap, nD_cap, k_cap, pad2;
+};
+
+struct SiteWork {
+  int site;                // global site index
+  int mpo;                 // PT-MPO index
+  int lam;                 // global lambda index of the bond left of the site
+  int pad;
+};

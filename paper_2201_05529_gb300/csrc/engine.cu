@@ -1,0 +1,974 @@
+// Host engine and C ABI of the PT-TEBD step (see include/pt_tebd.h).
+//
+// One handle holds every chain of a batch. Device state lives in capacity-sized buffers whose
+// live dimensions (chi per bond, kappa per site) are read by the kernels from device memory, so a
+// whole step -- three bond layers, the PT site layer, three bond layers, readout -- is one fixed
+// launch sequence that can be captured as a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "../../include/pt_tebd.h"
+
+using cplx = std::complex<double>;
+
+namespace {
+
+pt_alloc_fn g_alloc = nullptr;
+pt_free_fn g_free = nullptr;
+void* g_ctx = nullptr;
+thread_local std::string g_err;
+
+struct HostChain {
+  int N;
+  std::vector<cplx> rho0;                 // N*4
+  std::vector<cplx> gq, gh;               // (N-1)*256
+  std::vector<cplx> local_prop;           // N*16 or empty
+  std::vector<int> mpo;                   // N
+  std::vector<int> chi0, kappa0;          // optional
+  std::vector<std::vector<cplx>> gamma0;  // optional
+  std::vector<std::vector<double>> lambda0;
+};
+
+struct HostMpo {
+  int K;
+  std::vector<int> kappa;                 // K+1
+  std::vector<std::vector<cplx>> P;       // K tensors
+};
+
+struct Alloc {
+  void* p;
+  size_t bytes;
+};
+
+}  // namespace
+
+struct pt_tebd {
+  cudaStream_t stream = nullptr;
+  pt_options opt{};
+  std::string err;
+  std::vector<Alloc> allocs;
+
+  // problem copy (for clone)
+  std::vector<HostChain> chains;
+  std::vector<HostMpo> mpos_in;
+
+  // layout
+  int n_chains = 0, n_sites = 0, n_lams = 0, n_max = 0;
+  std::vector<int> site0, lam0;
+  std::vector<int> lam_cap_h;
+  std::vector<size_t> site_cap_h;
+  std::vector<int> kcap_h;            // per site
+  std::vector<int> site_mpo_h;        // per site (after fusion)
+  int n_mpos = 0;                     // device PT-MPOs (after fusion)
+  int K_limit = 0;
+
+  // device tables
+  Tables T{};
+  std::vector<double2*> gam_a, gam_b;  // host copies of the buffer pointers (primary/secondary)
+  std::vector<double*> lam_buf;
+  BondWork* d_odd = nullptr;
+  BondWork* d_even = nullptr;
+  int n_odd = 0, n_even = 0;
+  int gx_bond = 1;
+  SiteWork* d_sites = nullptr;
+  int n_site_work = 0;
+  int gx_site = 1;
+
+  // observables
+  double2* d_ops = nullptr;
+  int n_ops = 0;
+  double2* d_hist = nullptr;
+  double2* d_hist_tr = nullptr;
+  int hist_cap = 0;
+  double2* d_ops_now = nullptr;
+  double2* d_obs_now = nullptr;
+  double2* d_tr_now = nullptr;
+  double2* d_Lbuf = nullptr;
+  double2* d_Rbuf = nullptr;
+  int ld = 1;
+  static constexpr int MAX_OPS = 16;
+
+  int steps_done = 0;
+  cudaGraphExec_t graph = nullptr;
+  bool timing = false;
+  double stage_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  size_t ev_used = 0;
+
+  int fail(int code, const std::string& msg) {
+    err = msg;
+    g_err = msg;
+    return code;
+  }
+
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (g_alloc) {
+      p = g_alloc(bytes, g_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      p = nullptr;
+    }
+    if (p) allocs.push_back({p, bytes});
+    return p;
+  }
+
+  void release() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    for (auto& e : ev) {
+      cudaEventDestroy(e.second.first);
+      cudaEventDestroy(e.second.second);
+    }
+    ev.clear();
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto& a : allocs) {
+      if (g_free) g_free(a.p, g_ctx);
+      else cudaFree(a.p);
+    }
+    allocs.clear();
+  }
+};
+
+namespace {
+
+template <class T>
+T* upload(pt_tebd* h, const T* src, size_t n) {
+  T* d = (T*)h->dalloc(sizeof(T) * n);
+  if (!d) return nullptr;
+  if (n && cudaMemcpyAsync(d, src, sizeof(T) * n, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return nullptr;
+  return d;
+}
+
+template <class T>
+T* upload(pt_tebd* h, const std::vector<T>& v) {
+  return upload(h, v.data(), v.size());
+}
+
+int check_cuda(pt_tebd* h, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return h->fail(PT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return PT_OK;
+}
+
+int read_status(pt_tebd* h) {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, h->T.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->fail(PT_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(e));
+  if (st & ST_CAPACITY) return h->fail(PT_ERR_CAPACITY, "device: live dimension exceeded a buffer capacity");
+  if (st & ST_SVD_NOCONV) return h->fail(PT_ERR_SVD_NOCONV, "device: Jacobi SVD did not converge within max_sweeps");
+  if (st & ST_NAN) return h->fail(PT_ERR_NAN, "device: NaN in singular values or norms");
+  if (st & ST_PT_RANGE) return h->fail(PT_ERR_STEPS, "device: step beyond the PT-MPO length");
+  return PT_OK;
+}
+
+// ---------------------------------------------------------------- timing helpers
+void ev_begin(pt_tebd* h, int cat, cudaEvent_t* end_out) {
+  if (!h->timing) return;
+  if (h->ev_used == h->ev.size()) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    h->ev.push_back({cat, {a, b}});
+  }
+  auto& e = h->ev[h->ev_used++];
+  e.first = cat;
+  cudaEventRecord(e.second.first, h->stream);
+  *end_out = e.second.second;
+}
+void ev_end(pt_tebd* h, cudaEvent_t e) {
+  if (h->timing) cudaEventRecord(e, h->stream);
+}
+
+// ---------------------------------------------------------------- the step launch sequence
+void enqueue_layer(pt_tebd* h, const BondWork* work, int n) {
+  if (n == 0) return;
+  cudaStream_t s = h->stream;
+  cudaEvent_t e = nullptr;
+  ev_begin(h, 1, &e);
+  ptk::k_build_blocks<<<dim3(h->gx_bond, n), 256, 0, s>>>(h->T, work, n);
+  ptk::k_householder<<<dim3(n, 2), ptk::QR_THREADS_, 0, s>>>(h->T, work, n);
+  ev_end(h, e);
+  ev_begin(h, 2, &e);
+  ptk::k_theta_gate<<<dim3(h->gx_bond, n), 128, 0, s>>>(h->T, work, n);
+  ev_end(h, e);
+  ev_begin(h, 3, &e);
+  ptk::k_jacobi<<<n, ptk::JAC_THREADS_, 0, s>>>(work, n, h->opt.max_sweeps, h->T.status);
+  ev_end(h, e);
+  ev_begin(h, 4, &e);
+  ptk::k_truncate<<<(n + 63) / 64, 64, 0, s>>>(h->T, work, n, h->opt.chi_max, h->opt.eps,
+                                                h->opt.multiplet_tol);
+  ev_end(h, e);
+  ev_begin(h, 5, &e);
+  ptk::k_recover<<<dim3(h->gx_bond, n), 256, 0, s>>>(h->T, work, n);
+  ev_end(h, e);
+}
+
+void enqueue_chain_half(pt_tebd* h) {
+  enqueue_layer(h, h->d_odd, h->n_odd);
+  enqueue_layer(h, h->d_even, h->n_even);
+  enqueue_layer(h, h->d_odd, h->n_odd);
+}
+
+void enqueue_observe_history(pt_tebd* h) {
+  if (h->n_ops == 0) return;
+  cudaEvent_t e = nullptr;
+  ev_begin(h, 6, &e);
+  ptk::k_observe<<<h->n_chains, 256, 0, h->stream>>>(h->T, h->n_chains, h->d_ops, h->n_ops, h->n_max,
+                                                     h->d_hist, h->d_hist_tr, h->d_Lbuf, h->d_Rbuf,
+                                                     h->ld, 1);
+  ev_end(h, e);
+}
+
+void enqueue_step(pt_tebd* h) {
+  enqueue_chain_half(h);
+  if (h->n_site_work > 0) {
+    cudaEvent_t e = nullptr;
+    ev_begin(h, 0, &e);
+    ptk::k_site_contract<<<dim3(h->gx_site, h->n_site_work), 256, 0, h->stream>>>(h->T, h->d_sites,
+                                                                                 h->n_site_work);
+    ptk::k_site_swap<<<(h->n_site_work + 127) / 128, 128, 0, h->stream>>>(h->T, h->d_sites,
+                                                                          h->n_site_work);
+    ev_end(h, e);
+  }
+  enqueue_chain_half(h);
+  ptk::k_step_inc<<<1, 1, 0, h->stream>>>(h->T.step);
+  enqueue_observe_history(h);
+}
+
+int capture_graph(pt_tebd* h) {
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  cudaGraph_t g;
+  cudaStream_t cap;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+    return h->fail(PT_ERR_CUDA, "graph: stream create");
+  cudaStream_t keep = h->stream;
+  h->stream = cap;
+  bool t = h->timing;
+  h->timing = false;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    enqueue_step(h);
+    e = cudaStreamEndCapture(cap, &g);
+  }
+  h->stream = keep;
+  h->timing = t;
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) return h->fail(PT_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return h->fail(PT_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return PT_OK;
+}
+
+// ---------------------------------------------------------------- problem copy
+int copy_problem(pt_tebd* h, const pt_chain_desc* chains, int n_chains, const pt_mpo_desc* mpos,
+                 int n_mpos) {
+  h->chains.resize(n_chains);
+  for (int c = 0; c < n_chains; ++c) {
+    const pt_chain_desc& d = chains[c];
+    HostChain& hc = h->chains[c];
+    if (d.N < 1) return h->fail(PT_ERR_ARG, "chain N must be >= 1");
+    hc.N = d.N;
+    const bool has_mps = d.gamma0 != nullptr;
+    if (!has_mps && !d.rho0) return h->fail(PT_ERR_ARG, "chain needs rho0 or gamma0");
+    if (d.N > 1 && (!d.gates_q || !d.gates_h)) return h->fail(PT_ERR_ARG, "chain needs gates");
+    if (!has_mps) hc.rho0.assign((const cplx*)d.rho0, (const cplx*)d.rho0 + 4 * d.N);
+    if (d.N > 1) {
+      hc.gq.assign((const cplx*)d.gates_q, (const cplx*)d.gates_q + 256 * (d.N - 1));
+      hc.gh.assign((const cplx*)d.gates_h, (const cplx*)d.gates_h + 256 * (d.N - 1));
+    }
+    if (d.local_prop) hc.local_prop.assign((const cplx*)d.local_prop, (const cplx*)d.local_prop + 16 * d.N);
+    hc.mpo.assign(d.N, -1);
+    if (d.ptmpo_id)
+      for (int n = 0; n < d.N; ++n) {
+        hc.mpo[n] = d.ptmpo_id[n];
+        if (hc.mpo[n] >= n_mpos || hc.mpo[n] < -1) return h->fail(PT_ERR_ARG, "ptmpo_id out of range");
+      }
+    if (has_mps) {
+      if (!d.chi0 || !d.kappa0 || !d.lambda0) return h->fail(PT_ERR_ARG, "gamma0 needs chi0, kappa0, lambda0");
+      hc.chi0.assign(d.chi0, d.chi0 + d.N + 1);
+      hc.kappa0.assign(d.kappa0, d.kappa0 + d.N);
+      if (hc.chi0[0] != 1 || hc.chi0[d.N] != 1) return h->fail(PT_ERR_ARG, "chi0 ends must be 1");
+      for (int n = 0; n < d.N; ++n) {
+        if (hc.chi0[n] < 1 || hc.kappa0[n] < 1) return h->fail(PT_ERR_ARG, "chi0/kappa0 must be >= 1");
+        size_t sz = (size_t)hc.chi0[n] * 4 * hc.kappa0[n] * hc.chi0[n + 1];
+        hc.gamma0.emplace_back((const cplx*)d.gamma0[n], (const cplx*)d.gamma0[n] + sz);
+      }
+      for (int n = 0; n <= d.N; ++n)
+        hc.lambda0.emplace_back(d.lambda0[n], d.lambda0[n] + hc.chi0[n]);
+    }
+  }
+  h->mpos_in.resize(n_mpos);
+  for (int m = 0; m < n_mpos; ++m) {
+    const pt_mpo_desc& d = mpos[m];
+    if (d.K < 1 || !d.kappa || !d.P) return h->fail(PT_ERR_ARG, "PT-MPO needs K >= 1, kappa, P");
+    HostMpo& hm = h->mpos_in[m];
+    hm.K = d.K;
+    hm.kappa.assign(d.kappa, d.kappa + d.K + 1);
+    for (int k = 0; k < d.K; ++k) {
+      if (hm.kappa[k] < 1 || hm.kappa[k + 1] < 1) return h->fail(PT_ERR_ARG, "PT-MPO kappa must be >= 1");
+      size_t sz = (size_t)hm.kappa[k] * 16 * hm.kappa[k + 1];
+      hm.P.emplace_back((const cplx*)d.P[k], (const cplx*)d.P[k] + sz);
+    }
+  }
+  return PT_OK;
+}
+
+// Fuse an on-site propagator LP (applied after P) into a PT-MPO: P~[a,p,p',b] = sum_q LP[p',q] P[a,p,q,b].
+HostMpo fuse(const HostMpo& in, const cplx* LP) {
+  HostMpo out = in;
+  for (int k = 0; k < in.K; ++k) {
+    const int ka = in.kappa[k], kb = in.kappa[k + 1];
+    for (int a = 0; a < ka; ++a)
+      for (int p = 0; p < 4; ++p)
+        for (int pp = 0; pp < 4; ++pp)
+          for (int b = 0; b < kb; ++b) {
+            cplx s = 0;
+            for (int q = 0; q < 4; ++q) s += LP[pp * 4 + q] * in.P[k][((size_t)(a * 4 + p) * 4 + q) * kb + b];
+            out.P[k][((size_t)(a * 4 + p) * 4 + pp) * kb + b] = s;
+          }
+  }
+  return out;
+}
+
+// ---------------------------------------------------------------- build the device state
+int build(pt_tebd* h) {
+  const int C = (int)h->chains.size();
+  h->n_chains = C;
+  // device PT-MPO list: the shared ones, then per-site fused copies where a local propagator is given
+  std::vector<HostMpo> dm = h->mpos_in;
+  std::vector<std::vector<int>> site_m(C);
+  int K_limit = h->opt.max_steps > 0 ? h->opt.max_steps : 1024;
+  bool any_mpo = false;
+  for (int c = 0; c < C; ++c) {
+    HostChain& hc = h->chains[c];
+    site_m[c].assign(hc.N, -1);
+    for (int n = 0; n < hc.N; ++n) {
+      int m = hc.mpo[n];
+      if (!hc.local_prop.empty()) {
+        const cplx* LP = hc.local_prop.data() + 16 * n;
+        HostMpo base;
+        if (m >= 0) {
+          base = h->mpos_in[m];
+        } else {
+          base.K = K_limit;
+          base.kappa.assign(K_limit + 1, 1);
+          std::vector<cplx> id(16, 0.0);
+          for (int p = 0; p < 4; ++p) id[p * 4 + p] = 1.0;
+          base.P.assign(K_limit, id);
+        }
+        dm.push_back(fuse(base, LP));
+        m = (int)dm.size() - 1;
+      }
+      site_m[c][n] = m;
+    }
+  }
+  for (int c = 0; c < C; ++c)
+    for (int n = 0; n < h->chains[c].N; ++n)
+      if (site_m[c][n] >= 0) {
+        any_mpo = true;
+        K_limit = std::min(K_limit, dm[site_m[c][n]].K);
+      }
+  if (!any_mpo) K_limit = h->opt.max_steps > 0 ? h->opt.max_steps : 1024;
+  h->K_limit = K_limit;
+  h->n_mpos = (int)dm.size();
+
+  // layout and capacities
+  h->site0.resize(C);
+  h->lam0.resize(C);
+  h->n_sites = 0;
+  h->n_lams = 0;
+  h->n_max = 0;
+  for (int c = 0; c < C; ++c) {
+    h->site0[c] = h->n_sites;
+    h->lam0[c] = h->n_lams;
+    h->n_sites += h->chains[c].N;
+    h->n_lams += h->chains[c].N + 1;
+    h->n_max = std::max(h->n_max, h->chains[c].N);
+  }
+  h->kcap_h.assign(h->n_sites, 1);
+  h->site_mpo_h.assign(h->n_sites, -1);
+  h->lam_cap_h.assign(h->n_lams, 1);
+  h->site_cap_h.assign(h->n_sites, 0);
+  std::vector<int> kap_init(h->n_sites, 1), chi_init(h->n_lams, 1);
+  const double BIG = 1e9;
+  for (int c = 0; c < C; ++c) {
+    HostChain& hc = h->chains[c];
+    const int N = hc.N;
+    for (int n = 0; n < N; ++n) {
+      const int s = h->site0[c] + n;
+      const int m = site_m[c][n];
+      h->site_mpo_h[s] = m;
+      int kc = 1;
+      if (m >= 0)
+        for (int k = 0; k <= dm[m].K; ++k) kc = std::max(kc, dm[m].kappa[k]);
+      if (!hc.kappa0.empty()) {
+        kc = std::max(kc, hc.kappa0[n]);
+        kap_init[s] = hc.kappa0[n];
+        if (m >= 0 && dm[m].kappa[0] != hc.kappa0[n])
+          return h->fail(PT_ERR_ARG, "PT-MPO kappa[0] does not match the site's initial kappa");
+      } else if (m >= 0 && dm[m].kappa[0] != 1) {
+        return h->fail(PT_ERR_ARG, "PT-MPO kappa[0] must be 1 for a product initial state");
+      }
+      h->kcap_h[s] = kc;
+    }
+    // Liouville counting bound on each bond, capped at chi_max
+    for (int b = 0; b <= N; ++b) {
+      double L = 1, R = 1;
+      for (int i = 0; i < b; ++i) L = std::min(BIG, L * 4.0 * h->kcap_h[h->site0[c] + i]);
+      for (int i = b; i < N; ++i) R = std::min(BIG, R * 4.0 * h->kcap_h[h->site0[c] + i]);
+      int cap = (int)std::min((double)h->opt.chi_max, std::min(L, R));
+      if (b == 0 || b == N) cap = 1;
+      if (!hc.chi0.empty()) {
+        cap = std::max(cap, hc.chi0[b]);
+        chi_init[h->lam0[c] + b] = hc.chi0[b];
+      }
+      h->lam_cap_h[h->lam0[c] + b] = std::max(1, cap);
+    }
+    for (int n = 0; n < N; ++n) {
+      const int s = h->site0[c] + n, B = h->lam0[c] + n;
+      h->site_cap_h[s] = (size_t)h->lam_cap_h[B] * 4 * h->kcap_h[s] * h->lam_cap_h[B + 1];
+    }
+  }
+
+  // Gamma and lambda buffers
+  h->gam_a.resize(h->n_sites);
+  h->gam_b.resize(h->n_sites);
+  for (int s = 0; s < h->n_sites; ++s) {
+    h->gam_a[s] = (double2*)h->dalloc(sizeof(double2) * h->site_cap_h[s]);
+    h->gam_b[s] = (double2*)h->dalloc(sizeof(double2) * h->site_cap_h[s]);
+    if (!h->gam_a[s] || !h->gam_b[s]) return h->fail(PT_ERR_OOM, "Gamma buffers");
+  }
+  h->lam_buf.resize(h->n_lams);
+  int maxchi = 1;
+  for (int B = 0; B < h->n_lams; ++B) {
+    h->lam_buf[B] = (double*)h->dalloc(sizeof(double) * h->lam_cap_h[B]);
+    if (!h->lam_buf[B]) return h->fail(PT_ERR_OOM, "lambda buffers");
+    maxchi = std::max(maxchi, h->lam_cap_h[B]);
+  }
+  // initial state
+  for (int c = 0; c < C; ++c) {
+    HostChain& hc = h->chains[c];
+    for (int n = 0; n < hc.N; ++n) {
+      const int s = h->site0[c] + n;
+      std::vector<cplx> g;
+      if (hc.gamma0.empty()) g.assign(hc.rho0.begin() + 4 * n, hc.rho0.begin() + 4 * n + 4);
+      else g = hc.gamma0[n];
+      cudaMemcpyAsync(h->gam_a[s], g.data(), sizeof(cplx) * g.size(), cudaMemcpyHostToDevice, h->stream);
+    }
+    for (int b = 0; b <= hc.N; ++b) {
+      const int B = h->lam0[c] + b;
+      std::vector<double> l = hc.lambda0.empty() ? std::vector<double>{1.0} : hc.lambda0[b];
+      cudaMemcpyAsync(h->lam_buf[B], l.data(), sizeof(double) * l.size(), cudaMemcpyHostToDevice, h->stream);
+    }
+  }
+
+  // PT-MPOs and caps
+  std::vector<int> mK(h->n_mpos), kap_off(h->n_mpos), P_off(h->n_mpos), cap_off(h->n_mpos);
+  std::vector<int> kap_all;
+  std::vector<const double2*> P_ptrs;
+  std::vector<double2*> cap_ptrs;
+  for (int m = 0; m < h->n_mpos; ++m) {
+    mK[m] = dm[m].K;
+    kap_off[m] = (int)kap_all.size();
+    kap_all.insert(kap_all.end(), dm[m].kappa.begin(), dm[m].kappa.end());
+    P_off[m] = (int)P_ptrs.size();
+    size_t tot = 0;
+    for (auto& p : dm[m].P) tot += p.size();
+    double2* blob = (double2*)h->dalloc(sizeof(double2) * tot);
+    if (!blob) return h->fail(PT_ERR_OOM, "PT-MPO tensors");
+    size_t off = 0;
+    for (auto& p : dm[m].P) {
+      cudaMemcpyAsync(blob + off, p.data(), sizeof(cplx) * p.size(), cudaMemcpyHostToDevice, h->stream);
+      P_ptrs.push_back(blob + off);
+      off += p.size();
+    }
+    cap_off[m] = (int)cap_ptrs.size();
+    int kmax = 1;
+    for (int k : dm[m].kappa) kmax = std::max(kmax, k);
+    double2* cb = (double2*)h->dalloc(sizeof(double2) * (size_t)(dm[m].K + 1) * kmax);
+    if (!cb) return h->fail(PT_ERR_OOM, "caps");
+    for (int k = 0; k <= dm[m].K; ++k) cap_ptrs.push_back(cb + (size_t)k * kmax);
+  }
+
+  // device tables
+  Tables& T = h->T;
+  std::vector<size_t> scap(h->site_cap_h);
+  T.site_gam = upload(h, h->gam_a);
+  T.site_alt = upload(h, h->gam_b);
+  T.site_kappa = upload(h, kap_init);
+  T.site_mpo = upload(h, h->site_mpo_h);
+  T.site_cap = upload(h, scap);
+  T.lam_ptr = upload(h, h->lam_buf);
+  T.lam_chi = upload(h, chi_init);
+  T.lam_cap = upload(h, h->lam_cap_h);
+  std::vector<double> zeros(h->n_lams, 0.0);
+  T.lam_lognorm = upload(h, zeros);
+  std::vector<int> Nv(C);
+  for (int c = 0; c < C; ++c) Nv[c] = h->chains[c].N;
+  T.chain_site0 = upload(h, h->site0);
+  T.chain_lam0 = upload(h, h->lam0);
+  T.chain_N = upload(h, Nv);
+  std::vector<int> one{0};
+  T.mpo_K = upload(h, mK.empty() ? one : mK);
+  T.mpo_kappa_off = upload(h, kap_off.empty() ? one : kap_off);
+  T.mpo_kappa = upload(h, kap_all.empty() ? one : kap_all);
+  T.mpo_P_off = upload(h, P_off.empty() ? one : P_off);
+  std::vector<const double2*> nullp{nullptr};
+  T.mpo_P = upload(h, P_ptrs.empty() ? nullp : P_ptrs);
+  T.mpo_cap_off = upload(h, cap_off.empty() ? one : cap_off);
+  std::vector<double2*> nullc{nullptr};
+  T.mpo_cap = upload(h, cap_ptrs.empty() ? nullc : cap_ptrs);
+  T.step = upload(h, one);
+  T.status = upload(h, one);
+  if (!T.site_gam || !T.site_alt || !T.site_kappa || !T.site_mpo || !T.site_cap || !T.lam_ptr ||
+      !T.lam_chi || !T.lam_cap || !T.lam_lognorm || !T.chain_site0 || !T.chain_lam0 ||
+      !T.chain_N || !T.mpo_K || !T.mpo_kappa_off || !T.mpo_kappa || !T.mpo_P_off || !T.mpo_P ||
+      !T.mpo_cap_off || !T.mpo_cap || !T.step || !T.status)
+    return h->fail(PT_ERR_OOM, "device tables");
+  if (h->n_mpos > 0) ptk::k_caps<<<h->n_mpos, 128, 0, h->stream>>>(T, h->n_mpos);
+
+  // bond work lists (odd: 0-based bonds 0,2,..; even: 1,3,..) with private scratch
+  std::vector<BondWork> odd, even;
+  size_t max_bond_elems = 1;
+  for (int c = 0; c < C; ++c) {
+    HostChain& hc = h->chains[c];
+    double2* gq = hc.N > 1 ? upload(h, (const double2*)hc.gq.data(), hc.gq.size()) : nullptr;
+    double2* gh = hc.N > 1 ? upload(h, (const double2*)hc.gh.data(), hc.gh.size()) : nullptr;
+    if (hc.N > 1 && (!gq || !gh)) return h->fail(PT_ERR_OOM, "gates");
+    for (int b = 0; b + 1 < hc.N; ++b) {
+      BondWork W{};
+      W.chain = c;
+      W.site_l = h->site0[c] + b;
+      W.lam_l = h->lam0[c] + b;
+      const bool is_odd = (b % 2) == 0;
+      W.gate = (is_odd ? gq : gh) + 256 * b;
+      const int sL = W.site_l, sR = sL + 1, BL = W.lam_l;
+      const int chl = h->lam_cap_h[BL], chc = h->lam_cap_h[BL + 1], chr = h->lam_cap_h[BL + 2];
+      W.mL_cap = chl * h->kcap_h[sL];
+      W.nL_cap = 4 * chc;
+      W.mR_cap = 4 * chc;
+      W.nR_cap = h->kcap_h[sR] * chr;
+      const int rL = std::min(W.mL_cap, W.nL_cap), rR = std::min(W.mR_cap, W.nR_cap);
+      W.mD_cap = 4 * rL;
+      W.nD_cap = 4 * rR;
+      W.k_cap = std::min(W.mD_cap, W.nD_cap);
+      size_t qls = (size_t)W.mL_cap * W.nL_cap, rls = (size_t)W.nL_cap * W.nL_cap;
+      size_t qrs = (size_t)W.nR_cap * W.mR_cap, lrs = (size_t)W.mR_cap * W.mR_cap;
+      size_t as = (size_t)W.mD_cap * W.nD_cap, vs = (size_t)W.k_cap * W.k_cap;
+      W.QL = (double2*)h->dalloc(sizeof(double2) * qls);
+      W.RL = (double2*)h->dalloc(sizeof(double2) * rls);
+      W.QR = (double2*)h->dalloc(sizeof(double2) * qrs);
+      W.LR = (double2*)h->dalloc(sizeof(double2) * lrs);
+      W.HH = (double2*)h->dalloc(sizeof(double2) * (qls + qrs));
+      W.A = (double2*)h->dalloc(sizeof(double2) * as);
+      W.V = (double2*)h->dalloc(sizeof(double2) * vs);
+      W.sig = (double*)h->dalloc(sizeof(double) * W.k_cap);
+      W.aux = (double*)h->dalloc(sizeof(double) * W.k_cap);
+      W.perm = (int*)h->dalloc(sizeof(int) * W.k_cap);
+      W.info = (int*)h->dalloc(sizeof(int) * 4);
+      if (!W.QL || !W.RL || !W.QR || !W.LR || !W.HH || !W.A || !W.V || !W.sig || !W.aux || !W.perm || !W.info)
+        return h->fail(PT_ERR_OOM, "bond scratch");
+      cudaMemsetAsync(W.info, 0, sizeof(int) * 4, h->stream);
+      if (W.nL_cap > 2048 || W.mR_cap > 2048)
+        return h->fail(PT_ERR_CAPACITY, "QR reduction supports at most 2048 columns (4 chi <= 2048)");
+      max_bond_elems = std::max(max_bond_elems, std::max(qls + qrs, as));
+      (is_odd ? odd : even).push_back(W);
+    }
+  }
+  h->n_odd = (int)odd.size();
+  h->n_even = (int)even.size();
+  h->d_odd = odd.empty() ? nullptr : upload(h, odd);
+  h->d_even = even.empty() ? nullptr : upload(h, even);
+  h->gx_bond = (int)std::min<size_t>(256, (max_bond_elems + 255) / 256);
+
+  // site work list
+  std::vector<SiteWork> sw;
+  size_t max_site = 1;
+  for (int c = 0; c < C; ++c)
+    for (int n = 0; n < h->chains[c].N; ++n) {
+      const int s = h->site0[c] + n;
+      if (h->site_mpo_h[s] < 0) continue;
+      sw.push_back({s, h->site_mpo_h[s], h->lam0[c] + n, 0});
+      max_site = std::max(max_site, h->site_cap_h[s]);
+    }
+  h->n_site_work = (int)sw.size();
+  h->d_sites = sw.empty() ? nullptr : upload(h, sw);
+  h->gx_site = (int)std::min<size_t>(256, (max_site + 255) / 256);
+
+  // readout buffers
+  h->ld = maxchi;
+  h->d_Lbuf = (double2*)h->dalloc(sizeof(double2) * (size_t)C * (h->n_max + 1) * h->ld);
+  h->d_Rbuf = (double2*)h->dalloc(sizeof(double2) * (size_t)C * (h->n_max + 1) * h->ld);
+  h->d_ops_now = (double2*)h->dalloc(sizeof(double2) * 4 * pt_tebd::MAX_OPS);
+  h->d_obs_now = (double2*)h->dalloc(sizeof(double2) * (size_t)C * h->n_max * pt_tebd::MAX_OPS);
+  h->d_tr_now = (double2*)h->dalloc(sizeof(double2) * C);
+  h->hist_cap = h->K_limit + 1;
+  if (!h->d_Lbuf || !h->d_Rbuf || !h->d_ops_now || !h->d_obs_now || !h->d_tr_now)
+    return h->fail(PT_ERR_OOM, "readout buffers");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "init");
+  return check_cuda(h, "init");
+}
+
+void op_vectors(const double* ops, int n_ops, std::vector<cplx>& out) {
+  // vec(O^T)[i*2+j] = O[j][i]
+  out.resize(4 * (size_t)n_ops);
+  const cplx* O = (const cplx*)ops;
+  for (int k = 0; k < n_ops; ++k)
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) out[4 * k + i * 2 + j] = O[4 * k + j * 2 + i];
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+extern "C" {
+
+void pt_tebd_set_allocator(pt_alloc_fn alloc, pt_free_fn free_fn, void* ctx) {
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_ctx = ctx;
+}
+
+const char* pt_tebd_last_error(pt_tebd_t h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+int pt_tebd_init(pt_tebd_t* out, const pt_chain_desc* chains, int n_chains, const pt_mpo_desc* mpos,
+                 int n_mpos, const pt_options* opt, void* cuda_stream) {
+  if (!out || !chains || n_chains < 1 || !opt || (n_mpos > 0 && !mpos) || n_mpos < 0) {
+    g_err = "pt_tebd_init: bad arguments";
+    return PT_ERR_ARG;
+  }
+  *out = nullptr;
+  pt_tebd* h = new pt_tebd();
+  h->stream = (cudaStream_t)cuda_stream;
+  h->opt = *opt;
+  if (h->opt.chi_max < 1 || !(h->opt.eps >= 0.0) || h->opt.multiplet_tol < 0.0) {
+    h->fail(PT_ERR_ARG, "pt_tebd_init: chi_max >= 1, eps >= 0, multiplet_tol >= 0 required");
+    delete h;
+    return PT_ERR_ARG;
+  }
+  if (h->opt.max_sweeps <= 0) h->opt.max_sweeps = 60;
+  if (h->opt.precision != PT_FP64) {
+    h->fail(PT_ERR_ARG, "pt_tebd_init: this build supports PT_FP64 only");
+    delete h;
+    return PT_ERR_ARG;
+  }
+  int rc = copy_problem(h, chains, n_chains, mpos, n_mpos);
+  if (rc == PT_OK) rc = build(h);
+  if (rc == PT_OK && h->opt.use_graph) rc = capture_graph(h);
+  if (rc != PT_OK) {
+    g_err = h->err;
+    h->release();
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return PT_OK;
+}
+
+int pt_tebd_set_observables(pt_tebd_t h, const double* ops, int n_ops) {
+  if (!h || n_ops < 0 || n_ops > pt_tebd::MAX_OPS || (n_ops > 0 && !ops))
+    return h ? h->fail(PT_ERR_ARG, "set_observables: 0 <= n_ops <= 16") : PT_ERR_ARG;
+  std::vector<cplx> v;
+  op_vectors(ops, n_ops, v);
+  if (!h->d_ops) {
+    h->d_ops = (double2*)h->dalloc(sizeof(double2) * 4 * pt_tebd::MAX_OPS);
+    if (!h->d_ops) return h->fail(PT_ERR_OOM, "ops");
+  }
+  if (h->d_hist && h->n_ops != n_ops) return h->fail(PT_ERR_ARG, "set_observables: op count is fixed once set");
+  if (!h->d_hist && n_ops > 0) {
+    const size_t n = (size_t)h->hist_cap * h->n_chains * h->n_max * n_ops;
+    h->d_hist = (double2*)h->dalloc(sizeof(double2) * n);
+    h->d_hist_tr = (double2*)h->dalloc(sizeof(double2) * (size_t)h->hist_cap * h->n_chains);
+    if (!h->d_hist || !h->d_hist_tr) return h->fail(PT_ERR_OOM, "history");
+    cudaMemsetAsync(h->d_hist, 0, sizeof(double2) * n, h->stream);
+    cudaMemsetAsync(h->d_hist_tr, 0, sizeof(double2) * (size_t)h->hist_cap * h->n_chains, h->stream);
+  }
+  if (n_ops > 0) cudaMemcpyAsync(h->d_ops, v.data(), sizeof(cplx) * v.size(), cudaMemcpyHostToDevice, h->stream);
+  h->n_ops = n_ops;
+  // record the current step, and re-capture the step graph so it includes the readout
+  enqueue_observe_history(h);
+  int rc = check_cuda(h, "set_observables");
+  if (rc == PT_OK && h->opt.use_graph) rc = capture_graph(h);
+  return rc;
+}
+
+int pt_tebd_step(pt_tebd_t h, int n_steps) {
+  if (!h || n_steps < 0) return PT_ERR_ARG;
+  if (h->steps_done + n_steps > h->K_limit)
+    return h->fail(PT_ERR_STEPS, "step: past the end of the PT-MPOs / history capacity");
+  h->ev_used = 0;
+  for (int i = 0; i < n_steps; ++i) {
+    if (h->graph && !h->timing) {
+      if (cudaGraphLaunch(h->graph, h->stream) != cudaSuccess) return check_cuda(h, "graph launch");
+    } else {
+      enqueue_step(h);
+    }
+  }
+  h->steps_done += n_steps;
+  if (h->timing) {
+    cudaStreamSynchronize(h->stream);
+    for (int k = 0; k < 7; ++k) h->stage_ms[k] = 0;
+    for (size_t i = 0; i < h->ev_used; ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, h->ev[i].second.first, h->ev[i].second.second);
+      h->stage_ms[h->ev[i].first] += ms;
+    }
+  }
+  return check_cuda(h, "step");
+}
+
+int pt_tebd_sync(pt_tebd_t h) {
+  if (!h) return PT_ERR_ARG;
+  int rc = check_cuda(h, "sync");
+  if (rc != PT_OK) return rc;
+  return read_status(h);
+}
+
+int pt_tebd_observe(pt_tebd_t h, const double* ops, int n_ops, double* out, double* trace_out,
+                    int normalize) {
+  if (!h || n_ops < 0 || n_ops > pt_tebd::MAX_OPS || (n_ops > 0 && (!ops || !out))) return PT_ERR_ARG;
+  std::vector<cplx> v;
+  op_vectors(ops, n_ops, v);
+  if (n_ops > 0) cudaMemcpyAsync(h->d_ops_now, v.data(), sizeof(cplx) * v.size(), cudaMemcpyHostToDevice, h->stream);
+  ptk::k_observe<<<h->n_chains, 256, 0, h->stream>>>(h->T, h->n_chains, h->d_ops_now, n_ops, h->n_max,
+                                                     h->d_obs_now, h->d_tr_now, h->d_Lbuf, h->d_Rbuf,
+                                                     h->ld, 0);
+  int rc = check_cuda(h, "observe");
+  if (rc != PT_OK) return rc;
+  const size_t n = (size_t)h->n_chains * h->n_max * n_ops;
+  std::vector<cplx> o(n), tr(h->n_chains);
+  cudaMemcpyAsync(o.data(), h->d_obs_now, sizeof(cplx) * n, cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(tr.data(), h->d_tr_now, sizeof(cplx) * h->n_chains, cudaMemcpyDeviceToHost, h->stream);
+  rc = read_status(h);
+  if (rc != PT_OK) return rc;
+  for (int c = 0; c < h->n_chains; ++c) {
+    const cplx t = tr[c];
+    for (size_t i = 0; i < (size_t)h->n_max * n_ops; ++i) {
+      cplx x = o[(size_t)c * h->n_max * n_ops + i];
+      if (normalize) x /= t;
+      ((cplx*)out)[(size_t)c * h->n_max * n_ops + i] = x;
+    }
+  }
+  if (trace_out) std::memcpy(trace_out, tr.data(), sizeof(cplx) * h->n_chains);
+  return PT_OK;
+}
+
+int pt_tebd_read_history(pt_tebd_t h, int first, int count, double* out, double* trace_out) {
+  if (!h || first < 0 || count < 0 || first + count > h->hist_cap || !h->d_hist) return PT_ERR_ARG;
+  const size_t per = (size_t)h->n_chains * h->n_max * h->n_ops;
+  if (out)
+    cudaMemcpyAsync(out, h->d_hist + (size_t)first * per, sizeof(cplx) * per * count, cudaMemcpyDeviceToHost,
+                    h->stream);
+  if (trace_out)
+    cudaMemcpyAsync(trace_out, h->d_hist_tr + (size_t)first * h->n_chains, sizeof(cplx) * h->n_chains * count,
+                    cudaMemcpyDeviceToHost, h->stream);
+  return read_status(h);
+}
+
+int pt_tebd_apply_local(pt_tebd_t h, int chain, int site, const double* op2x2, int side) {
+  if (!h || chain < 0 || chain >= h->n_chains || site < 0 || site >= h->chains[chain].N || !op2x2 ||
+      (side != 0 && side != 1))
+    return h ? h->fail(PT_ERR_ARG, "apply_local: bad arguments") : PT_ERR_ARG;
+  const cplx* A = (const cplx*)op2x2;
+  cplx S[16];
+  // left: S = A (x) I ; right: S = I (x) A^T, in vec index p = i*2 + j
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      for (int k = 0; k < 2; ++k)
+        for (int l = 0; l < 2; ++l) {
+          const int p = i * 2 + j, q = k * 2 + l;
+          cplx v = 0;
+          if (side == 0) v = (j == l) ? A[i * 2 + k] : 0.0;
+          else v = (i == k) ? A[l * 2 + j] : 0.0;
+          S[p * 4 + q] = v;
+        }
+  ptk::launch_apply_local(h->T, h->site0[chain] + site, h->lam0[chain] + site, (const double2*)S, h->stream);
+  return check_cuda(h, "apply_local");
+}
+
+int pt_tebd_steps_done(pt_tebd_t h) { return h ? h->steps_done : PT_ERR_ARG; }
+
+int pt_tebd_get_dims(pt_tebd_t h, int chain, int* chi, int* kappa) {
+  if (!h || chain < 0 || chain >= h->n_chains) return PT_ERR_ARG;
+  const int N = h->chains[chain].N;
+  if (chi) cudaMemcpyAsync(chi, h->T.lam_chi + h->lam0[chain], sizeof(int) * (N + 1), cudaMemcpyDeviceToHost, h->stream);
+  if (kappa) cudaMemcpyAsync(kappa, h->T.site_kappa + h->site0[chain], sizeof(int) * N, cudaMemcpyDeviceToHost, h->stream);
+  return read_status(h);
+}
+
+int pt_tebd_get_lambda(pt_tebd_t h, int chain, int bond, double* out, int cap) {
+  if (!h || chain < 0 || chain >= h->n_chains || bond < 0 || bond > h->chains[chain].N || !out) return PT_ERR_ARG;
+  const int B = h->lam0[chain] + bond;
+  int chi = 0;
+  cudaMemcpyAsync(&chi, h->T.lam_chi + B, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  const int n = std::min(chi, cap);
+  cudaMemcpyAsync(out, h->lam_buf[B], sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+  int rc = read_status(h);
+  return rc == PT_OK ? chi : rc;
+}
+
+int pt_tebd_get_lognorm(pt_tebd_t h, int chain, double* out) {
+  if (!h || chain < 0 || chain >= h->n_chains || !out) return PT_ERR_ARG;
+  const int N = h->chains[chain].N;
+  std::vector<double> v(N + 1);
+  cudaMemcpyAsync(v.data(), h->T.lam_lognorm + h->lam0[chain], sizeof(double) * (N + 1), cudaMemcpyDeviceToHost,
+                  h->stream);
+  int rc = read_status(h);
+  double s = 0;
+  for (double x : v) s += x;
+  *out = s;
+  return rc;
+}
+
+int pt_tebd_clone(pt_tebd_t h, pt_tebd_t* out) {
+  if (!h || !out) return PT_ERR_ARG;
+  *out = nullptr;
+  int rc = read_status(h);
+  if (rc != PT_OK) return rc;
+  pt_tebd* c = new pt_tebd();
+  c->stream = h->stream;
+  c->opt = h->opt;
+  c->chains = h->chains;
+  c->mpos_in = h->mpos_in;
+  rc = build(c);
+  if (rc != PT_OK) {
+    g_err = c->err;
+    c->release();
+    delete c;
+    return rc;
+  }
+  // copy the live state: current Gamma buffers, lambdas, dims, log-norms, step, history
+  std::vector<double2*> cur(h->n_sites);
+  cudaMemcpyAsync(cur.data(), h->T.site_gam, sizeof(double2*) * h->n_sites, cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  for (int s = 0; s < h->n_sites; ++s)
+    cudaMemcpyAsync(c->gam_a[s], cur[s], sizeof(double2) * h->site_cap_h[s], cudaMemcpyDeviceToDevice, h->stream);
+  for (int B = 0; B < h->n_lams; ++B)
+    cudaMemcpyAsync(c->lam_buf[B], h->lam_buf[B], sizeof(double) * h->lam_cap_h[B], cudaMemcpyDeviceToDevice,
+                    h->stream);
+  cudaMemcpyAsync(c->T.lam_chi, h->T.lam_chi, sizeof(int) * h->n_lams, cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(c->T.lam_lognorm, h->T.lam_lognorm, sizeof(double) * h->n_lams, cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(c->T.site_kappa, h->T.site_kappa, sizeof(int) * h->n_sites, cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(c->T.step, h->T.step, sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
+  c->steps_done = h->steps_done;
+  cudaStreamSynchronize(h->stream);
+  rc = check_cuda(c, "clone");
+  if (rc == PT_OK && c->opt.use_graph) rc = capture_graph(c);
+  if (rc != PT_OK) {
+    c->release();
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return PT_OK;
+}
+
+int pt_tebd_destroy(pt_tebd_t h) {
+  if (!h) return PT_ERR_ARG;
+  h->release();
+  delete h;
+  return PT_OK;
+}
+
+int pt_tebd_set_timing(pt_tebd_t h, int enable) {
+  if (!h) return PT_ERR_ARG;
+  h->timing = enable != 0;
+  return PT_OK;
+}
+
+int pt_tebd_get_timing(pt_tebd_t h, double* ms7) {
+  if (!h || !ms7) return PT_ERR_ARG;
+  for (int k = 0; k < 7; ++k) ms7[k] = h->stage_ms[k];
+  return PT_OK;
+}
+
+// ---------------------------------------------------------------- standalone batched SVD
+static size_t svd_layout(int m, int n, int batch, size_t* offs) {
+  const int Ma = std::max(m, n), Na = std::min(m, n);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o += (bytes + 255) & ~size_t(255);
+    return r;
+  };
+  offs[0] = take(sizeof(double2) * (size_t)Ma * Na * batch);  // A
+  offs[1] = take(sizeof(double2) * (size_t)Na * Na * batch);  // V
+  offs[2] = take(sizeof(double) * (size_t)Na * batch);        // sig
+  offs[3] = take(sizeof(int) * (size_t)Na * batch);           // perm
+  offs[4] = take(sizeof(int) * (size_t)batch);                // info (sweeps)
+  offs[5] = take(sizeof(int));                                // status
+  return o;
+}
+
+size_t pt_svd_scratch_bytes(int m, int n, int batch) {
+  if (m < 1 || n < 1 || batch < 1) return 0;
+  size_t offs[6];
+  return svd_layout(m, n, batch, offs);
+}
+
+int pt_svd_f64(const double* A, int m, int n, int batch, double* sigma, double* U, double* V,
+               void* scratch, int max_sweeps, void* cuda_stream) {
+  if (!A || m < 1 || n < 1 || batch < 1 || !sigma || !U || !V || !scratch) {
+    g_err = "pt_svd_f64: bad arguments";
+    return PT_ERR_ARG;
+  }
+  if (max_sweeps <= 0) max_sweeps = 60;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  size_t offs[6];
+  svd_layout(m, n, batch, offs);
+  char* base = (char*)scratch;
+  double2* wA = (double2*)(base + offs[0]);
+  double2* wV = (double2*)(base + offs[1]);
+  double* sig = (double*)(base + offs[2]);
+  int* perm = (int*)(base + offs[3]);
+  int* info = (int*)(base + offs[4]);
+  int* status = (int*)(base + offs[5]);
+  const int Ma = std::max(m, n), Na = std::min(m, n);
+  const size_t sA = (size_t)Ma * Na, sV = (size_t)Na * Na;
+  cudaMemsetAsync(status, 0, sizeof(int), st);
+  const int gx = (int)std::min<size_t>(256, ((size_t)m * n + 255) / 256);
+  ptk::k_svd_load<<<dim3(gx, batch), 256, 0, st>>>((const double2*)A, m, n, batch, wA, sA);
+  ptk::k_svd_batched<<<batch, ptk::JAC_THREADS_, 0, st>>>(wA, wV, sig, perm, info, m, n, batch, sA, sV,
+                                                          max_sweeps, status);
+  const int gs = (int)std::min<size_t>(256, ((size_t)(m + n + 1) * Na + 255) / 256);
+  ptk::k_svd_store<<<dim3(gs, batch), 256, 0, st>>>(wA, wV, sig, perm, m, n, batch, sA, sV, sigma,
+                                                    (double2*)U, (double2*)V);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_err = std::string("pt_svd_f64: ") + cudaGetErrorString(e);
+    return PT_ERR_CUDA;
+  }
+  int hs = 0;
+  e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    g_err = std::string("pt_svd_f64: ") + cudaGetErrorString(e);
+    return PT_ERR_CUDA;
+  }
+  if (hs & ST_SVD_NOCONV) {
+    g_err = "pt_svd_f64: Jacobi did not converge";
+    return PT_ERR_SVD_NOCONV;
+  }
+  if (hs & ST_NAN) {
+    g_err = "pt_svd_f64: NaN";
+    return PT_ERR_NAN;
+  }
+  return PT_OK;
+}
+
+}  // extern "C"
