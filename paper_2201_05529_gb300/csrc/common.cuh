@@ -86,7 +86,7 @@ struct BondWork {
   double* sig;             // [k_cap] singular values (unsorted)
   double* aux;             // [k_cap] column norms scratch
   int* perm;               // [k_cap] perm[rank] = column
-  int* info;               // [4] per-item: 0 mD, 1 nD, 2 transposed, 3 sweeps
+  int* info;               // [8] per-item: 0 mD, 1 nD, 2 transposed, 3 sweeps, 4-5 rotation counters
   int mL_cap, nL_cap, mR_cap, nR_cap, mD_cap, nD_cap, k_cap, pad2;
 };
 

@@ -76,6 +76,7 @@ struct pt_tebd {
   BondWork* d_even = nullptr;
   int n_odd = 0, n_even = 0;
   int gx_bond = 1;
+  int cl_odd = 1, cl_even = 1;        // Jacobi cluster sizes per layer list
   SiteWork* d_sites = nullptr;
   int n_site_work = 0;
   int gx_site = 1;
@@ -202,7 +203,8 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n) {
   ptk::k_theta_gate<<<dim3(h->gx_bond, n), 128, 0, s>>>(h->T, work, n);
   ev_end(h, e);
   ev_begin(h, 3, &e);
-  ptk::k_jacobi<<<n, ptk::JAC_THREADS_, 0, s>>>(work, n, h->opt.max_sweeps, h->T.status);
+  ptk::launch_jacobi_cluster(work, n, work == h->d_odd ? h->cl_odd : h->cl_even, h->opt.max_sweeps,
+                             h->T.status, s);
   ev_end(h, e);
   ev_begin(h, 4, &e);
   ptk::k_truncate<<<(n + 63) / 64, 64, 0, s>>>(h->T, work, n, h->opt.chi_max, h->opt.eps,
@@ -579,10 +581,10 @@ int build(pt_tebd* h) {
       W.sig = (double*)h->dalloc(sizeof(double) * W.k_cap);
       W.aux = (double*)h->dalloc(sizeof(double) * W.k_cap);
       W.perm = (int*)h->dalloc(sizeof(int) * W.k_cap);
-      W.info = (int*)h->dalloc(sizeof(int) * 4);
+      W.info = (int*)h->dalloc(sizeof(int) * 8);
       if (!W.QL || !W.RL || !W.QR || !W.LR || !W.HH || !W.A || !W.V || !W.sig || !W.aux || !W.perm || !W.info)
         return h->fail(PT_ERR_OOM, "bond scratch");
-      cudaMemsetAsync(W.info, 0, sizeof(int) * 4, h->stream);
+      cudaMemsetAsync(W.info, 0, sizeof(int) * 8, h->stream);
       if (W.nL_cap > 2048 || W.mR_cap > 2048)
         return h->fail(PT_ERR_CAPACITY, "QR reduction supports at most 2048 columns (4 chi <= 2048)");
       max_bond_elems = std::max(max_bond_elems, std::max(qls + qrs, as));
@@ -591,6 +593,14 @@ int build(pt_tebd* h) {
   }
   h->n_odd = (int)odd.size();
   h->n_even = (int)even.size();
+  // cluster size: about 8 column pairs per CTA of 32 warps, at most 16 CTAs per matrix
+  auto pick = [&](const std::vector<BondWork>& v) {
+    int k = 1;
+    for (auto& W : v) k = std::max(k, W.k_cap);
+    return ptk::jacobi_cluster_size(std::max(1, std::min(16, (k / 2 + 7) / 8)));
+  };
+  h->cl_odd = pick(odd);
+  h->cl_even = pick(even);
   h->d_odd = odd.empty() ? nullptr : upload(h, odd);
   h->d_even = even.empty() ? nullptr : upload(h, even);
   h->gx_bond = (int)std::min<size_t>(256, (max_bond_elems + 255) / 256);
@@ -910,14 +920,16 @@ static size_t svd_layout(int m, int n, int batch, size_t* offs) {
   offs[1] = take(sizeof(double2) * (size_t)Na * Na * batch);  // V
   offs[2] = take(sizeof(double) * (size_t)Na * batch);        // sig
   offs[3] = take(sizeof(int) * (size_t)Na * batch);           // perm
-  offs[4] = take(sizeof(int) * (size_t)batch);                // info (sweeps)
+  offs[4] = take(sizeof(int) * 8 * (size_t)batch);            // info
   offs[5] = take(sizeof(int));                                // status
+  offs[6] = take(sizeof(BondWork) * (size_t)batch);           // work items
+  offs[7] = take(sizeof(double) * (size_t)Na * batch);        // column norms
   return o;
 }
 
 size_t pt_svd_scratch_bytes(int m, int n, int batch) {
   if (m < 1 || n < 1 || batch < 1) return 0;
-  size_t offs[6];
+  size_t offs[8];
   return svd_layout(m, n, batch, offs);
 }
 
@@ -929,7 +941,7 @@ int pt_svd_f64(const double* A, int m, int n, int batch, double* sigma, double* 
   }
   if (max_sweeps <= 0) max_sweeps = 60;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  size_t offs[6];
+  size_t offs[8];
   svd_layout(m, n, batch, offs);
   char* base = (char*)scratch;
   double2* wA = (double2*)(base + offs[0]);
@@ -938,16 +950,43 @@ int pt_svd_f64(const double* A, int m, int n, int batch, double* sigma, double* 
   int* perm = (int*)(base + offs[3]);
   int* info = (int*)(base + offs[4]);
   int* status = (int*)(base + offs[5]);
+  BondWork* items = (BondWork*)(base + offs[6]);
   const int Ma = std::max(m, n), Na = std::min(m, n);
   const size_t sA = (size_t)Ma * Na, sV = (size_t)Na * Na;
+  std::vector<BondWork> hw(batch);
+  std::vector<int> hinfo(8 * (size_t)batch, 0);
+  for (int b = 0; b < batch; ++b) {
+    BondWork W{};
+    W.A = wA + b * sA;
+    W.V = wV + b * sV;
+    W.sig = sig + (size_t)b * Na;
+    W.perm = perm + (size_t)b * Na;
+    W.info = info + 8 * (size_t)b;
+    W.aux = (double*)(base + offs[7]) + (size_t)b * Na;
+    W.mD_cap = m;
+    W.nD_cap = n;
+    W.k_cap = Na;
+    hw[b] = W;
+    hinfo[8 * b + 0] = m;
+    hinfo[8 * b + 1] = n;
+    hinfo[8 * b + 2] = m < n ? 1 : 0;
+  }
+  cudaMemcpyAsync(items, hw.data(), sizeof(BondWork) * batch, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(info, hinfo.data(), sizeof(int) * hinfo.size(), cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(status, 0, sizeof(int), st);
   const int gx = (int)std::min<size_t>(256, ((size_t)m * n + 255) / 256);
   ptk::k_svd_load<<<dim3(gx, batch), 256, 0, st>>>((const double2*)A, m, n, batch, wA, sA);
-  ptk::k_svd_batched<<<batch, ptk::JAC_THREADS_, 0, st>>>(wA, wV, sig, perm, info, m, n, batch, sA, sV,
-                                                          max_sweeps, status);
+  const int cl = ptk::jacobi_cluster_size(std::max(1, std::min(16, (Na / 2 + 7) / 8)));
+  ptk::launch_jacobi_cluster(items, batch, cl, max_sweeps, status, st);
   const int gs = (int)std::min<size_t>(256, ((size_t)(m + n + 1) * Na + 255) / 256);
   ptk::k_svd_store<<<dim3(gs, batch), 256, 0, st>>>(wA, wV, sig, perm, m, n, batch, sA, sV, sigma,
                                                     (double2*)U, (double2*)V);
+  // the host copies of items/info must outlive the async copies above
+  cudaError_t es = cudaStreamSynchronize(st);
+  if (es != cudaSuccess) {
+    g_err = std::string("pt_svd_f64: ") + cudaGetErrorString(es);
+    return PT_ERR_CUDA;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     g_err = std::string("pt_svd_f64: ") + cudaGetErrorString(e);

@@ -5,7 +5,6 @@
 namespace ptk {
 
 constexpr int QR_THREADS_ = 512;
-constexpr int JAC_THREADS_ = 1024;
 
 struct Super4;
 
@@ -14,7 +13,6 @@ __global__ void k_site_swap(Tables T, const SiteWork* work, int n_work);
 __global__ void k_build_blocks(Tables T, const BondWork* work, int n_work);
 __global__ void k_householder(Tables T, const BondWork* work, int n_work);
 __global__ void k_theta_gate(Tables T, const BondWork* work, int n_work);
-__global__ void k_jacobi(const BondWork* work, int n_work, int max_sweeps, int* status);
 __global__ void k_truncate(Tables T, const BondWork* work, int n_work, int chi_max, double eps,
                            double mtol);
 __global__ void k_recover(Tables T, const BondWork* work, int n_work);
@@ -25,12 +23,14 @@ __global__ void k_observe(Tables T, int n_chains, const double2* ops, int n_ops,
 __global__ void k_step_inc(int* step);
 __global__ void k_svd_load(const double2* A, int m, int n, int batch, double2* work_A,
                            size_t strideA);
-__global__ void k_svd_batched(double2* work_A, double2* work_V, double* sig, int* perm, int* info,
-                              int m, int n, int batch, size_t strideA, size_t strideV,
-                              int max_sweeps, int* status);
 __global__ void k_svd_store(const double2* work_A, const double2* work_V, const double* sig,
                             const int* perm, int m, int n, int batch, size_t strideA,
                             size_t strideV, double* sigma_out, double2* U, double2* V);
+
+// cluster-parallel FP64 bond SVD (jacobi_cluster.cu)
+int jacobi_cluster_size(int want);
+void launch_jacobi_cluster(const BondWork* work, int n_work, int cluster, int max_sweeps, int* status,
+                           cudaStream_t st);
 
 // local super-operator launch (struct passed by value lives in the kernel TU)
 void launch_apply_local(const Tables& T, int site, int lam, const double2* s16, cudaStream_t st);

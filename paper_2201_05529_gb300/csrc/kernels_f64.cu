@@ -306,123 +306,8 @@ __global__ void k_theta_gate(Tables T, const BondWork* work, int n_work) {
   }
 }
 
-// ------------------------------------------------------------------ K4: one-sided Jacobi SVD
-// Hestenes one-sided Jacobi in FP64 on a column-major Ma x Na matrix (Ma >= Na): columns are
-// rotated pairwise until every pair is orthogonal to tol * sqrt(|a_i|^2 |a_j|^2). Pairs follow a
-// round-robin tournament so each round is a set of disjoint pairs, one warp per pair. On exit
-// A holds U (normalised columns), V the right factor, sig the column norms, perm the order by
-// descending sigma.
-constexpr int JAC_THREADS = 1024;
-
-PT_DEV void jacobi_pair(double2* A, double2* V, int Ma, int Na, int i, int j, double tol,
-                        int lane, int* rot) {
-  const double2* ai = A + (size_t)i * Ma;
-  const double2* aj = A + (size_t)j * Ma;
-  double al = 0.0, be = 0.0;
-  double2 ga = cmk(0, 0);
-  for (int r = lane; r < Ma; r += 32) {
-    const double2 x = ai[r], y = aj[r];
-    al += cabs2(x);
-    be += cabs2(y);
-    ga = cfma_conj(x, y, ga);
-  }
-  al = warp_sum(al);
-  be = warp_sum(be);
-  ga.x = warp_sum(ga.x);
-  ga.y = warp_sum(ga.y);
-  const double g = sqrt(cabs2(ga));
-  if (!(g > tol * sqrt(al * be)) || g == 0.0) return;
-  const double zeta = (be - al) / (2.0 * g);
-  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-  const double2 e = cscale(cconj(ga), 1.0 / g);   // e^{-i phi}
-  const double2 se = cscale(e, s), ce = cscale(e, c);
-  double2* Ai = A + (size_t)i * Ma;
-  double2* Aj = A + (size_t)j * Ma;
-  for (int r = lane; r < Ma; r += 32) {
-    const double2 x = Ai[r], y = Aj[r];
-    Ai[r] = csub(cscale(x, c), cmul(se, y));
-    Aj[r] = cadd(cscale(x, s), cmul(ce, y));
-  }
-  double2* Vi = V + (size_t)i * Na;
-  double2* Vj = V + (size_t)j * Na;
-  for (int r = lane; r < Na; r += 32) {
-    const double2 x = Vi[r], y = Vj[r];
-    Vi[r] = csub(cscale(x, c), cmul(se, y));
-    Vj[r] = cadd(cscale(x, s), cmul(ce, y));
-  }
-  if (lane == 0) atomicAdd(rot, 1);
-}
-
-PT_DEV void jacobi_svd(double2* A, double2* V, double* sig, int* perm, int Ma, int Na,
-                       int max_sweeps, int* sweeps_out, int* status) {
-  __shared__ int rot;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  for (size_t idx = tid; idx < (size_t)Na * Na; idx += blockDim.x)
-    V[idx] = ((idx % Na) == (idx / Na)) ? cmk(1, 0) : cmk(0, 0);
-  const double tol = (double)Ma * 1.1102230246251565e-16;
-  const int Np = Na + (Na & 1);
-  int sweep = 0;
-  bool converged = (Na < 2);
-  __syncthreads();
-  while (!converged && sweep < max_sweeps) {
-    if (tid == 0) rot = 0;
-    __syncthreads();
-    for (int round = 0; round < Np - 1; ++round) {
-      for (int q = wid; q < Np / 2; q += nw) {
-        int i, j;
-        if (q == 0) { i = Np - 1; j = round; }
-        else { i = (round + q) % (Np - 1); j = (round - q + Np - 1) % (Np - 1); }
-        if (i > j) { const int t = i; i = j; j = t; }
-        if (j >= Na) continue;
-        jacobi_pair(A, V, Ma, Na, i, j, tol, lane, &rot);
-      }
-      __syncthreads();
-    }
-    ++sweep;
-    converged = (rot == 0);
-    __syncthreads();
-  }
-  if (!converged && tid == 0) atomicOr(status, ST_SVD_NOCONV);
-  if (tid == 0) *sweeps_out = converged ? sweep : -sweep;
-  // column norms, normalise
-  for (int c = wid; c < Na; c += nw) {
-    double2* a = A + (size_t)c * Ma;
-    double s2 = 0.0;
-    for (int r = lane; r < Ma; r += 32) s2 += cabs2(a[r]);
-    s2 = warp_sum(s2);
-    const double s = sqrt(s2);
-    if (lane == 0) sig[c] = s;
-    if (s > 0.0) {
-      const double inv = 1.0 / s;
-      for (int r = lane; r < Ma; r += 32) a[r] = cscale(a[r], inv);
-    }
-    if (lane == 0 && !(s == s)) atomicOr(status, ST_NAN);
-  }
-  __syncthreads();
-  for (int c = tid; c < Na; c += blockDim.x) {
-    const double sc = sig[c];
-    int rank = 0;
-    for (int k = 0; k < Na; ++k) {
-      const double sk = sig[k];
-      rank += (sk > sc) || (sk == sc && k < c);
-    }
-    perm[rank] = c;
-  }
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(JAC_THREADS) k_jacobi(const BondWork* work, int n_work,
-                                                        int max_sweeps, int* status) {
-  const int w = blockIdx.x;
-  if (w >= n_work) return;
-  const BondWork& W = work[w];
-  const int mD = W.info[0], nD = W.info[1];
-  if (mD <= 0 || nD <= 0) return;
-  const bool tr = W.info[2] != 0;
-  const int Ma = tr ? nD : mD, Na = tr ? mD : nD;
-  jacobi_svd(W.A, W.V, W.sig, W.perm, Ma, Na, max_sweeps, W.info + 3, status);
-}
+// ------------------------------------------------------------------ K4: the SVD of D
+// The one-sided Jacobi SVD runs as a cluster-parallel kernel (jacobi_cluster.cu).
 
 // ------------------------------------------------------------------ K5: truncation
 // App. A.2: the smallest chi with ||discarded||_2 < eps * s_max, capped at chi_max; exact zeros
@@ -720,7 +605,8 @@ __global__ void k_step_inc(int* step) { *step += 1; }
 
 // ------------------------------------------------------------------ standalone batched SVD
 // For the kernel-level entry point: load row-major A_b (m x n) into column-major (or the
-// conjugate transpose when m < n), run the Jacobi, write sigma (descending), U, V row-major.
+// conjugate transpose when m < n); after the cluster Jacobi, write sigma (descending), U, V
+// row-major.
 __global__ void k_svd_load(const double2* A, int m, int n, int batch, double2* work_A,
                            size_t strideA) {
   const int b = blockIdx.y;
@@ -734,19 +620,6 @@ __global__ void k_svd_load(const double2* A, int m, int n, int batch, double2* w
     if (!tr) work_A[b * strideA + i + (size_t)j * Ma] = v;
     else work_A[b * strideA + j + (size_t)i * Ma] = cconj(v);
   }
-}
-
-__global__ void __launch_bounds__(JAC_THREADS) k_svd_batched(double2* work_A, double2* work_V,
-                                                             double* sig, int* perm, int* info,
-                                                             int m, int n, int batch,
-                                                             size_t strideA, size_t strideV,
-                                                             int max_sweeps, int* status) {
-  const int b = blockIdx.x;
-  if (b >= batch) return;
-  const bool tr = m < n;
-  const int Ma = tr ? n : m, Na = tr ? m : n;
-  jacobi_svd(work_A + b * strideA, work_V + b * strideV, sig + (size_t)b * Na,
-             perm + (size_t)b * Na, Ma, Na, max_sweeps, info + b, status);
 }
 
 __global__ void k_svd_store(const double2* work_A, const double2* work_V, const double* sig,

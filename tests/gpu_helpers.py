@@ -56,3 +56,21 @@ def run_oracle(w, cis, ops, K=None, insert=None, multiplet_tol=1e-12):
 
 
 OPS = [model.SZ, model.SX, model.SY]
+
+
+def oracle_envelope(w, ci, ops, K=None, scale=1e-13, seed=1, insert=None):
+    """Rounding sensitivity of the oracle's own trajectory: |run(inputs) - run(inputs perturbed by
+    `scale` relative noise on the dt/4 gates)| per step, as a running maximum over steps.
+
+    Once the chi cap binds, the kept singular values reach ~1e-9 of the largest and the lambda^-1
+    of the Gamma recovery (App. A.2 (g-h)) amplifies rounding differences step by step, up to the
+    accumulated truncation error; two correct FP64 implementations can then differ by this much.
+    """
+    rng = np.random.default_rng(seed)
+    gq = [g * (1 + scale * rng.standard_normal(g.shape)) for g in ci.gates_q]
+    ins = None if insert is None else (insert[1], insert[2], insert[3])
+    a = oprob.simulate_chain(ci, w, ops, K=K, insert=ins)
+    b = oprob.simulate_chain(oprob.ChainInputs(ci.N, ci.rho0, gq, ci.gates_h, ci.pt, ci.init_mps),
+                             w, ops, K=K, insert=ins)
+    d = np.abs(a.obs - b.obs).max(axis=(1, 2))
+    return np.maximum.accumulate(d)
