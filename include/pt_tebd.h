@@ -152,6 +152,22 @@ size_t pt_svd_scratch_bytes(int m, int n, int batch);
 int pt_svd_f64(const double* A, int m, int n, int batch, double* sigma, double* U, double* V,
                void* scratch, int max_sweeps, void* cuda_stream);
 
+/* ---- allocation-free variant of pt_svd_f64 (the paper has no counterpart) ----
+ * For callers that cannot allocate device memory: their device memory is owned by another pool
+ * (a framework that reserves the GPU up front, a fixed-budget service), or a device allocation is
+ * not acceptable where they run (cudaMalloc may synchronise the device and can fail mid-job).
+ * Same batched FP64 Jacobi SVD and the same arguments and outputs as pt_svd_f64, minus the
+ * scratch pointer: the workspace is a static device array of PT_SVD_NOALLOC_MAX_BYTES bytes that
+ * every GPU which loads this library holds until the process exits. A problem whose workspace
+ * (pt_svd_scratch_bytes(m, n, batch)) is larger is rejected with PT_ERR_CAPACITY. The first call on
+ * a device looks up the array's device address with that device current; make that first call
+ * before any stream capture. All calls share the one array: calls that overlap on the GPU race and
+ * corrupt each other, so the caller must serialise them. Each call clears what must start at zero
+ * and synchronises the stream before returning. Messages: pt_tebd_last_error(NULL). */
+#define PT_SVD_NOALLOC_MAX_BYTES ((size_t)16 << 20)
+int pt_svd_f64_noalloc(const double* A, int m, int n, int batch, double* sigma, double* U, double* V,
+                       int max_sweeps, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ EXPORTS = [
     "pt_tebd_observe", "pt_tebd_read_history", "pt_tebd_apply_local", "pt_tebd_steps_done",
     "pt_tebd_get_dims", "pt_tebd_get_lambda", "pt_tebd_get_lognorm", "pt_tebd_clone",
     "pt_tebd_sync", "pt_tebd_destroy", "pt_tebd_last_error", "pt_tebd_set_timing",
-    "pt_tebd_get_timing", "pt_svd_scratch_bytes", "pt_svd_f64",
+    "pt_tebd_get_timing", "pt_svd_scratch_bytes", "pt_svd_f64", "pt_svd_f64_noalloc",
 ]
 
 
@@ -37,7 +37,7 @@ class PTError(RuntimeError):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2201_05529_gb300.build.build()")
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2201_05529_gb300.build()")
     return C.CDLL(LIB_PATH)
 
 
@@ -91,6 +91,11 @@ lib.pt_svd_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
 lib.pt_svd_scratch_bytes.restype = C.c_size_t
 lib.pt_svd_f64.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                            C.c_void_p, C.c_int, C.c_void_p]
+
+
+lib.pt_svd_f64_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_int, C.c_void_p]
+NOALLOC_MAX_BYTES = 16 << 20     # PT_SVD_NOALLOC_MAX_BYTES
 
 
 def _check(rc, h=None):
@@ -298,4 +303,15 @@ def svd_f64(A, sigma, U, V, scratch, max_sweeps=0, stream=None):
     rc = lib.pt_svd_f64(C.c_void_p(A.data_ptr()), m, n, b, C.c_void_p(sigma.data_ptr()),
                         C.c_void_p(U.data_ptr()), C.c_void_p(V.data_ptr()),
                         C.c_void_p(scratch.data_ptr()), int(max_sweeps), st)
+    _check(rc, None)
+
+
+def svd_f64_noalloc(A, sigma, U, V, max_sweeps=0, stream=None):
+    """pt_svd_f64_noalloc: the same SVD as svd_f64 with no workspace argument. For callers that
+    cannot allocate device memory; the library's static workspace (NOALLOC_MAX_BYTES) is shared by
+    every call, so calls must not overlap on the GPU."""
+    b, m, n = A.shape
+    st = stream if stream is not None else current_stream_handle()
+    rc = lib.pt_svd_f64_noalloc(C.c_void_p(A.data_ptr()), m, n, b, C.c_void_p(sigma.data_ptr()),
+                                C.c_void_p(U.data_ptr()), C.c_void_p(V.data_ptr()), int(max_sweeps), st)
     _check(rc, None)

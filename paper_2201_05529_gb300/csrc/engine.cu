@@ -644,6 +644,10 @@ void op_vectors(const double* ops, int n_ops, std::vector<cplx>& out) {
 
 }  // namespace
 
+namespace ptk {
+void set_global_error(const char* msg) { g_err = msg; }
+}  // namespace ptk
+
 // ==================================================================== C ABI
 extern "C" {
 

@@ -32,6 +32,9 @@ int jacobi_cluster_size(int want);
 void launch_jacobi_cluster(const BondWork* work, int n_work, int cluster, int max_sweeps, int* status,
                            cudaStream_t st);
 
+// set the message returned by pt_tebd_last_error(NULL) (engine.cu)
+void set_global_error(const char* msg);
+
 // local super-operator launch (struct passed by value lives in the kernel TU)
 void launch_apply_local(const Tables& T, int site, int lam, const double2* s16, cudaStream_t st);
 
