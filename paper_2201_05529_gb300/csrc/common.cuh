@@ -39,6 +39,7 @@ enum : int {
   ST_SVD_NOCONV = 2,
   ST_NAN = 4,
   ST_PT_RANGE = 8,
+  ST_TIMEOUT = 16,
 };
 
 // ---------------------------------------------------------------- engine tables (device)

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -77,6 +78,10 @@ struct pt_tebd {
   int n_odd = 0, n_even = 0;
   int gx_bond = 1;
   int cl_odd = 1, cl_even = 1;        // Jacobi cluster sizes per layer list
+  int grid_blocks = 0;                // whole-GPU Jacobi: CTAs per launch (0: use the cluster kernel)
+  unsigned* d_sync3 = nullptr;        // grid barrier state
+  int* d_cnt_odd = nullptr;           // per-item rotation counters
+  int* d_cnt_even = nullptr;
   SiteWork* d_sites = nullptr;
   int n_site_work = 0;
   int gx_site = 1;
@@ -169,6 +174,7 @@ int read_status(pt_tebd* h) {
   if (st & ST_SVD_NOCONV) return h->fail(PT_ERR_SVD_NOCONV, "device: Jacobi SVD did not converge within max_sweeps");
   if (st & ST_NAN) return h->fail(PT_ERR_NAN, "device: NaN in singular values or norms");
   if (st & ST_PT_RANGE) return h->fail(PT_ERR_STEPS, "device: step beyond the PT-MPO length");
+  if (st & ST_TIMEOUT) return h->fail(PT_ERR_DEVICE_TIMEOUT, "device: a grid barrier wait ran out of time");
   return PT_OK;
 }
 
@@ -203,8 +209,12 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n) {
   ptk::k_theta_gate<<<dim3(h->gx_bond, n), 128, 0, s>>>(h->T, work, n);
   ev_end(h, e);
   ev_begin(h, 3, &e);
-  ptk::launch_jacobi_cluster(work, n, work == h->d_odd ? h->cl_odd : h->cl_even, h->opt.max_sweeps,
-                             h->T.status, s);
+  if (h->grid_blocks > 0)
+    ptk::launch_jacobi_grid(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3,
+                            work == h->d_odd ? h->d_cnt_odd : h->d_cnt_even, h->T.status, s);
+  else
+    ptk::launch_jacobi_cluster(work, n, work == h->d_odd ? h->cl_odd : h->cl_even, h->opt.max_sweeps,
+                               h->T.status, s);
   ev_end(h, e);
   ev_begin(h, 4, &e);
   ptk::k_truncate<<<(n + 63) / 64, 64, 0, s>>>(h->T, work, n, h->opt.chi_max, h->opt.eps,
@@ -601,6 +611,16 @@ int build(pt_tebd* h) {
   };
   h->cl_odd = pick(odd);
   h->cl_even = pick(even);
+  // bond SVDs: whole-GPU cooperative kernel by default; PT_TEBD_JACOBI=cluster selects one
+  // thread-block cluster per matrix instead
+  const char* jv = getenv("PT_TEBD_JACOBI");
+  const bool want_cluster = jv && std::string(jv) == "cluster";
+  h->grid_blocks = (!want_cluster && std::max(h->n_odd, h->n_even) <= 1024) ? ptk::jacobi_grid_blocks() : 0;
+  h->d_sync3 = (unsigned*)h->dalloc(sizeof(unsigned) * 4);
+  h->d_cnt_odd = (int*)h->dalloc(sizeof(int) * 2 * std::max(1, h->n_odd));
+  h->d_cnt_even = (int*)h->dalloc(sizeof(int) * 2 * std::max(1, h->n_even));
+  if (!h->d_sync3 || !h->d_cnt_odd || !h->d_cnt_even) return h->fail(PT_ERR_OOM, "Jacobi barrier state");
+  cudaMemsetAsync(h->d_sync3, 0, sizeof(unsigned) * 4, h->stream);
   h->d_odd = odd.empty() ? nullptr : upload(h, odd);
   h->d_even = even.empty() ? nullptr : upload(h, even);
   h->gx_bond = (int)std::min<size_t>(256, (max_bond_elems + 255) / 256);

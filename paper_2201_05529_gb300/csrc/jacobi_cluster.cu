@@ -49,12 +49,13 @@ __device__ __forceinline__ bool jac_pair(typename CT<R>::T* A, typename CT<R>::T
   be = wsum(be);
   gr = wsum(gr);
   gi = wsum(gi);
-  const R g = r_sqrt(gr * gr + gi * gi);
+  const R g2 = gr * gr + gi * gi;
   // columns at the rounding-noise level of the matrix (|a|^2 <= floor2) are not rotated: they can
   // never become orthogonal relative to their own norm and carry no information at this precision
-  if (!(g > tol * r_sqrt(al * be)) || g == R(0) || !(fmin(al, be) > floor2)) return false;
-  const R zeta = (be - al) / (R(2) * g);
-  const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + r_sqrt(R(1) + zeta * zeta));
+  if (!(g2 > tol * tol * al * be) || g2 == R(0) || !(fmin(al, be) > floor2)) return false;
+  const R g = r_sqrt(g2), h = be - al;
+  // tan(theta) = 2 g sign(h) / (|h| + sqrt(h^2 + 4 g^2)), the smaller root of the rotation equation
+  const R t = (h >= R(0) ? R(2) : R(-2)) * g / (fabs(h) + r_sqrt(h * h + R(4) * g2));
   const R c = R(1) / r_sqrt(R(1) + t * t), s = c * t;
   // e = exp(-i phi) = conj(gamma) / |gamma|
   const R er = gr / g, ei = -gi / g;

@@ -1,0 +1,389 @@
+// Whole-GPU one-sided Jacobi SVD for all bond matrices of one layer (App. A.2 (f-g)).
+//
+// The SVD is bound by FP64 arithmetic (1.2 TFLOP/s on GB300, ~7.9 GFLOP/s per SM), so every SM
+// must work on it even when a layer has only two bonds. One cooperative launch (one 1024-thread
+// CTA per SM) processes every matrix of the layer: in each round of the round-robin tournament the
+// column pairs of all matrices form one task list, each task handled by a group of 4 warps (one per
+// SM sub-partition) that split the rows; a grid barrier separates the rounds. Partial sums are
+// combined in a fixed order, so results are bitwise reproducible. Every barrier wait has a time
+// limit: on expiry the kernel records ST_TIMEOUT, raises an abort flag that releases every other
+// CTA, and returns.
+#include "kernels.h"
+
+namespace ptk {
+
+namespace {
+
+constexpr int GRID_THREADS = 1024;
+constexpr int GROUP_WARPS = 4;
+constexpr int GROUPS = GRID_THREADS / 32 / GROUP_WARPS;    // 8 pair tasks per CTA at a time
+constexpr int MAX_ITEMS = 1024;
+constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;       // ~2 s at 2 GHz
+
+struct GridSync {
+  unsigned* count;
+  unsigned* gen;
+  int* abort;
+};
+
+// Grid-wide barrier for a cooperative launch; false when aborted (timeout here or elsewhere).
+__device__ bool grid_barrier(const GridSync& gs, int* status) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = gs.gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(gs.count, 1u) == gridDim.x - 1) {
+      *gs.count = 0;
+      __threadfence();
+      atomicAdd(gs.gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (*(volatile int*)gs.abort) { ok = 0; break; }
+        if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+          atomicOr(status, ST_TIMEOUT);
+          atomicExch(gs.abort, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)gs.abort) ok = 0;
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+__device__ __forceinline__ double wsumd(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+struct ItemDims {
+  double2* A;
+  double2* V;
+  int Ma, Na, Np;
+};
+
+__device__ __forceinline__ ItemDims item_dims(const BondWork& W) {
+  ItemDims d;
+  const int mD = W.info[0], nD = W.info[1];
+  const bool tr = W.info[2] != 0;
+  d.A = W.A;
+  d.V = W.V;
+  d.Ma = (mD > 0 && nD > 0) ? (tr ? nD : mD) : 0;
+  d.Na = (mD > 0 && nD > 0) ? (tr ? mD : nD) : 0;
+  d.Np = d.Na + (d.Na & 1);
+  return d;
+}
+
+}  // namespace
+
+// work: layer items; sync: grid barrier state; cnt: [n_work][2] rotation counters.
+__global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* work, int n_work, int max_sweeps,
+                                                              GridSync gs, int* cnt, int* status) {
+  __shared__ int s_Na[MAX_ITEMS];
+  __shared__ int s_off[MAX_ITEMS + 1];      // prefix of pair counts of the active items this round
+  __shared__ unsigned char s_active[MAX_ITEMS];
+  __shared__ double s_part[GROUPS][GROUP_WARPS][4];
+  __shared__ double s_rot[GROUPS][8];       // rotate flag, c, s, s e^{-i phi}, c e^{-i phi}
+  __shared__ double s_fro[MAX_ITEMS];       // ||A||_F^2 per item (rounding-noise floor)
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int grp = wid / GROUP_WARPS, gw = wid % GROUP_WARPS;
+  const int n_groups = gridDim.x * GROUPS;
+  const int my_group = grp * gridDim.x + blockIdx.x;     // consecutive tasks go to different SMs
+  const double eps = 1.1102230246251565e-16;
+  if (n_work > MAX_ITEMS) {
+    if (blockIdx.x == 0 && tid == 0) atomicOr(status, ST_CAPACITY);
+    return;
+  }
+  for (int w = tid; w < n_work; w += blockDim.x) {
+    const ItemDims d = item_dims(work[w]);
+    s_Na[w] = d.Na;
+    s_active[w] = d.Na >= 2;
+  }
+  __syncthreads();
+  // V = I, zero counters, column norms (for the rounding-noise floor)
+  {
+    const int gt = blockIdx.x * blockDim.x + tid, ngt = gridDim.x * blockDim.x;
+    for (int w = 0; w < n_work; ++w) {
+      const int Na = s_Na[w];
+      double2* V = work[w].V;
+      for (size_t idx = gt; idx < (size_t)Na * Na; idx += ngt) {
+        double2 v;
+        v.x = ((idx % Na) == (idx / Na)) ? 1.0 : 0.0;
+        v.y = 0.0;
+        __stcg(V + idx, v);
+      }
+      if (gt == 0) {
+        cnt[2 * w] = 0;
+        cnt[2 * w + 1] = 0;
+      }
+    }
+    const int gwarp = wid * gridDim.x + blockIdx.x, ngwarp = gridDim.x * (blockDim.x / 32);
+    int base = 0;
+    for (int w = 0; w < n_work; ++w) {
+      const ItemDims d = item_dims(work[w]);
+      for (int c = gwarp - base; c < d.Na; c += ngwarp) {
+        if (c < 0) continue;
+        const double2* a = d.A + (size_t)c * d.Ma;
+        double s2 = 0;
+        for (int r = lane; r < d.Ma; r += 32) {
+          const double2 x = __ldcg(a + r);
+          s2 += x.x * x.x + x.y * x.y;
+        }
+        s2 = wsumd(s2);
+        if (lane == 0) __stcg(work[w].aux + c, s2);
+      }
+      base = (base + d.Na) % ngwarp;
+    }
+  }
+  if (!grid_barrier(gs, status)) return;
+  // ||A||_F^2 per item, summed in the same fixed order by every CTA
+  for (int w = wid; w < n_work; w += blockDim.x / 32) {
+    double acc = 0;
+    for (int k = lane; k < s_Na[w]; k += 32) acc += __ldcg(work[w].aux + k);
+    acc = wsumd(acc);
+    if (lane == 0) s_fro[w] = acc;
+  }
+  __syncthreads();
+  int sweep = 0;
+  bool any = false;
+  for (int w = 0; w < n_work; ++w) any |= s_active[w] != 0;
+  while (any && sweep < max_sweeps) {
+    const int par = sweep & 1;
+    if (blockIdx.x == 0)
+      for (int w = tid; w < n_work; w += blockDim.x) cnt[2 * w + (par ^ 1)] = 0;
+    // rounds: the longest active tournament sets the count
+    int rounds = 0;
+    for (int w = 0; w < n_work; ++w)
+      if (s_active[w]) rounds = max(rounds, s_Na[w] + (s_Na[w] & 1) - 1);
+    for (int round = 0; round < rounds; ++round) {
+      if (tid == 0) {
+        int o = 0;
+        for (int w = 0; w < n_work; ++w) {
+          s_off[w] = o;
+          const int Np = s_Na[w] + (s_Na[w] & 1);
+          if (s_active[w] && round < Np - 1) o += Np / 2;
+        }
+        s_off[n_work] = o;
+      }
+      __syncthreads();
+      const int total = s_off[n_work];
+      for (int t = my_group; t < total; t += n_groups) {
+        // item of task t (binary search over the offsets)
+        int lo = 0, hi = n_work - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        const int w = lo;
+        const int q = t - s_off[w];
+        const ItemDims d = item_dims(work[w]);
+        const int Np = d.Np;
+        int i, j;
+        if (q == 0) { i = Np - 1; j = round; }
+        else { i = (round + q) % (Np - 1); j = (round - q + Np - 1) % (Np - 1); }
+        if (i > j) { const int tt = i; i = j; j = tt; }
+        const bool real_pair = j < d.Na;      // uniform within the group
+        double al = 0, be = 0, gr = 0, gi = 0;
+        double2* ai = d.A + (size_t)i * d.Ma;
+        double2* aj = d.A + (size_t)j * d.Ma;
+        if (real_pair) {
+          for (int r = gw * 32 + lane; r < d.Ma; r += 32 * GROUP_WARPS) {
+            const double2 x = __ldcg(ai + r), y = __ldcg(aj + r);
+            al = fma(x.x, x.x, fma(x.y, x.y, al));
+            be = fma(y.x, y.x, fma(y.y, y.y, be));
+            gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+            gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+          }
+          al = wsumd(al);
+          be = wsumd(be);
+          gr = wsumd(gr);
+          gi = wsumd(gi);
+          if (lane == 0) {
+            s_part[grp][gw][0] = al;
+            s_part[grp][gw][1] = be;
+            s_part[grp][gw][2] = gr;
+            s_part[grp][gw][3] = gi;
+          }
+        }
+        named_sync(1 + grp, 32 * GROUP_WARPS);
+        // one lane turns the partial sums (fixed order) into the rotation and shares it
+        if (gw == 0 && lane == 0) {
+          double flag = 0.0, c = 1.0, sv = 0.0, ser = 0.0, sei = 0.0, cer = 1.0, cei = 0.0;
+          if (real_pair) {
+            al = be = gr = gi = 0;
+#pragma unroll
+            for (int k = 0; k < GROUP_WARPS; ++k) {
+              al += s_part[grp][k][0];
+              be += s_part[grp][k][1];
+              gr += s_part[grp][k][2];
+              gi += s_part[grp][k][3];
+            }
+            const double g2 = gr * gr + gi * gi;
+            const double tol = (double)d.Ma * eps;
+            // rotate unless |gamma| <= tol sqrt(alpha beta), or a column is at the noise floor
+            // (|a|^2 <= eps^2 ||A||_F^2, see the cluster kernel)
+            if (g2 > tol * tol * al * be && g2 > 0.0 && fmin(al, be) > eps * eps * s_fro[w]) {
+              const double g = sqrt(g2), h = be - al;
+              // tan(theta) = 2 g sign(h) / (|h| + sqrt(h^2 + 4 g^2)): the smaller root
+              const double t = (h >= 0.0 ? 2.0 : -2.0) * g / (fabs(h) + sqrt(h * h + 4.0 * g2));
+              c = rsqrt(1.0 + t * t);
+              sv = c * t;
+              const double sg = sv / g;              // s / |gamma|
+              ser = sg * gr;                          // s e^{-i phi}: e = conj(gamma) / |gamma|
+              sei = -sg * gi;
+              cer = c * gr / g;
+              cei = -c * gi / g;
+              flag = 1.0;
+            }
+          }
+          s_rot[grp][0] = flag;
+          s_rot[grp][1] = c;
+          s_rot[grp][2] = sv;
+          s_rot[grp][3] = ser;
+          s_rot[grp][4] = sei;
+          s_rot[grp][5] = cer;
+          s_rot[grp][6] = cei;
+        }
+        named_sync(1 + grp, 32 * GROUP_WARPS);
+        if (!real_pair || s_rot[grp][0] == 0.0) {
+          named_sync(1 + grp, 32 * GROUP_WARPS);
+          continue;
+        }
+        const double c = s_rot[grp][1], s = s_rot[grp][2], ser = s_rot[grp][3], sei = s_rot[grp][4];
+        const double cer = s_rot[grp][5], cei = s_rot[grp][6];
+        for (int r = gw * 32 + lane; r < d.Ma; r += 32 * GROUP_WARPS) {
+          const double2 x = __ldcg(ai + r), y = __ldcg(aj + r);
+          double2 nx, ny;
+          nx.x = c * x.x - (ser * y.x - sei * y.y);
+          nx.y = c * x.y - (ser * y.y + sei * y.x);
+          ny.x = s * x.x + (cer * y.x - cei * y.y);
+          ny.y = s * x.y + (cer * y.y + cei * y.x);
+          __stcg(ai + r, nx);
+          __stcg(aj + r, ny);
+        }
+        double2* vi = d.V + (size_t)i * d.Na;
+        double2* vj = d.V + (size_t)j * d.Na;
+        for (int r = gw * 32 + lane; r < d.Na; r += 32 * GROUP_WARPS) {
+          const double2 x = __ldcg(vi + r), y = __ldcg(vj + r);
+          double2 nx, ny;
+          nx.x = c * x.x - (ser * y.x - sei * y.y);
+          nx.y = c * x.y - (ser * y.y + sei * y.x);
+          ny.x = s * x.x + (cer * y.x - cei * y.y);
+          ny.y = s * x.y + (cer * y.y + cei * y.x);
+          __stcg(vi + r, nx);
+          __stcg(vj + r, ny);
+        }
+        if (gw == 0 && lane == 0) atomicAdd(&cnt[2 * w + par], 1);
+      }
+      if (!grid_barrier(gs, status)) return;
+    }
+    // sweep done: retire converged items (every CTA reads the same counters)
+    if (tid == 0)
+      for (int w = 0; w < n_work; ++w)
+        if (s_active[w] && *(volatile int*)&cnt[2 * w + par] == 0) {
+          s_active[w] = 0;
+          if (blockIdx.x == 0) work[w].info[3] = sweep + 1;
+        }
+    __syncthreads();
+    any = false;
+    for (int w = 0; w < n_work; ++w) any |= s_active[w] != 0;
+    ++sweep;
+    if (!grid_barrier(gs, status)) return;
+  }
+  if (any && blockIdx.x == 0 && tid == 0) {
+    atomicOr(status, ST_SVD_NOCONV);
+    for (int w = 0; w < n_work; ++w)
+      if (s_active[w]) work[w].info[3] = -sweep;
+  }
+  // singular values: column norms, normalise the columns (left vectors), then rank by sigma
+  {
+    const int gwarp = wid * gridDim.x + blockIdx.x, ngwarp = gridDim.x * (blockDim.x / 32);
+    int base = 0;
+    for (int w = 0; w < n_work; ++w) {
+      const ItemDims d = item_dims(work[w]);
+      for (int c = gwarp - base; c < d.Na; c += ngwarp) {
+        if (c < 0) continue;
+        double2* a = d.A + (size_t)c * d.Ma;
+        double s2 = 0;
+        for (int r = lane; r < d.Ma; r += 32) {
+          const double2 x = __ldcg(a + r);
+          s2 += x.x * x.x + x.y * x.y;
+        }
+        s2 = wsumd(s2);
+        const double sg = sqrt(s2);
+        if (lane == 0) __stcg(work[w].sig + c, sg);
+        if (sg > 0.0) {
+          const double inv = 1.0 / sg;
+          for (int r = lane; r < d.Ma; r += 32) {
+            double2 x = __ldcg(a + r);
+            x.x *= inv;
+            x.y *= inv;
+            __stcg(a + r, x);
+          }
+        }
+        if (lane == 0 && !(sg == sg)) atomicOr(status, ST_NAN);
+      }
+      base = (base + d.Na) % ngwarp;
+    }
+  }
+  if (!grid_barrier(gs, status)) return;
+  {
+    const int gt = blockIdx.x * blockDim.x + tid, ngt = gridDim.x * blockDim.x;
+    for (int w = 0; w < n_work; ++w) {
+      const int Na = s_Na[w];
+      const double* sig = work[w].sig;
+      for (int c = gt; c < Na; c += ngt) {
+        const double sc = __ldcg(sig + c);
+        int rk = 0;
+        for (int k = 0; k < Na; ++k) {
+          const double sk = __ldcg(sig + k);
+          rk += (sk > sc) || (sk == sc && k < c);
+        }
+        work[w].perm[rk] = c;
+      }
+    }
+  }
+}
+
+int jacobi_grid_blocks() {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_grid, GRID_THREADS, 0);
+  return per_sm >= 1 ? sms : 0;
+}
+
+void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3,
+                        int* cnt, int* status, cudaStream_t st) {
+  // barrier arrival count and abort flag start at zero for every launch (the generation never resets)
+  cudaMemsetAsync(sync3, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(sync3 + 2, 0, sizeof(unsigned), st);
+  GridSync gs{sync3, sync3 + 1, (int*)(sync3 + 2)};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks, 1, 1);
+  cfg.blockDim = dim3(GRID_THREADS, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_jacobi_grid, work, n_work, max_sweeps, gs, cnt, status);
+}
+
+}  // namespace ptk

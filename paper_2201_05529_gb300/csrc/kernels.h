@@ -32,6 +32,12 @@ int jacobi_cluster_size(int want);
 void launch_jacobi_cluster(const BondWork* work, int n_work, int cluster, int max_sweeps, int* status,
                            cudaStream_t st);
 
+// whole-GPU FP64 bond SVD (jacobi_grid.cu): blocks = one per SM (0 if not co-schedulable);
+// sync3: 3 words of device memory (arrival count, generation, abort flag); cnt: 2 ints per item
+int jacobi_grid_blocks();
+void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3,
+                        int* cnt, int* status, cudaStream_t st);
+
 // set the message returned by pt_tebd_last_error(NULL) (engine.cu)
 void set_global_error(const char* msg);
 
