@@ -87,6 +87,8 @@ struct BondWork {
   double* sig;             // [k_cap] singular values (unsorted)
   double* aux;             // [k_cap] column norms scratch
   int* perm;               // [k_cap] perm[rank] = column
+  void* TA;                // fast path: packed split planes of the theta operands (tc_theta.cu)
+  void* TB;
   int* info;               // [8] per-item: 0 mD, 1 nD, 2 transposed, 3 sweeps, 4-5 rotation counters
   int mL_cap, nL_cap, mR_cap, nR_cap, mD_cap, nD_cap, k_cap, pad2;
 };

@@ -79,6 +79,7 @@ struct pt_tebd {
   int gx_bond = 1;
   int cl_odd = 1, cl_even = 1;        // Jacobi cluster sizes per layer list
   int grid_blocks = 0;                // whole-GPU Jacobi: CTAs per launch (0: use the cluster kernel)
+  int rt_odd = 1, rt_even = 1, kc_odd = 1, kc_even = 1;   // fast path: theta tile / K-chunk caps
   unsigned* d_sync3 = nullptr;        // grid barrier state
   int* d_cnt_odd = nullptr;           // per-item rotation counters
   int* d_cnt_even = nullptr;
@@ -206,7 +207,11 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n) {
   ptk::k_householder<<<dim3(n, 2), ptk::QR_THREADS_, 0, s>>>(h->T, work, n);
   ev_end(h, e);
   ev_begin(h, 2, &e);
-  ptk::k_theta_gate<<<dim3(h->gx_bond, n), 128, 0, s>>>(h->T, work, n);
+  if (h->opt.precision == PT_FP64)
+    ptk::k_theta_gate<<<dim3(h->gx_bond, n), 128, 0, s>>>(h->T, work, n);
+  else
+    ptk::launch_tc_theta(h->T, work, n, work == h->d_odd ? h->rt_odd : h->rt_even,
+                         work == h->d_odd ? h->kc_odd : h->kc_even, (int)h->opt.precision, s);
   ev_end(h, e);
   ev_begin(h, 3, &e);
   if (h->grid_blocks > 0)
@@ -595,6 +600,12 @@ int build(pt_tebd* h) {
       if (!W.QL || !W.RL || !W.QR || !W.LR || !W.HH || !W.A || !W.V || !W.sig || !W.aux || !W.perm || !W.info)
         return h->fail(PT_ERR_OOM, "bond scratch");
       cudaMemsetAsync(W.info, 0, sizeof(int) * 8, h->stream);
+      if (h->opt.precision != PT_FP64) {
+        const int kcap = chc;
+        W.TA = h->dalloc(ptk::tc_pack_bytes(W.mD_cap, kcap, (int)h->opt.precision));
+        W.TB = h->dalloc(ptk::tc_pack_bytes(W.nD_cap, kcap, (int)h->opt.precision));
+        if (!W.TA || !W.TB) return h->fail(PT_ERR_OOM, "fast-path operand planes");
+      }
       if (W.nL_cap > 2048 || W.mR_cap > 2048)
         return h->fail(PT_ERR_CAPACITY, "QR reduction supports at most 2048 columns (4 chi <= 2048)");
       max_bond_elems = std::max(max_bond_elems, std::max(qls + qrs, as));
@@ -611,6 +622,18 @@ int build(pt_tebd* h) {
   };
   h->cl_odd = pick(odd);
   h->cl_even = pick(even);
+  if (h->opt.precision != PT_FP64) {
+    auto caps = [&](const std::vector<BondWork>& v, int* rt, int* kc) {
+      int rows = 1, k = 1;
+      for (auto& W : v) {
+        rows = std::max(rows, std::max(W.mD_cap, W.nD_cap));
+        k = std::max(k, W.nL_cap / 4);
+      }
+      ptk::tc_caps(rows, k, (int)h->opt.precision, rt, kc);
+    };
+    caps(odd, &h->rt_odd, &h->kc_odd);
+    caps(even, &h->rt_even, &h->kc_even);
+  }
   // bond SVDs: whole-GPU cooperative kernel by default; PT_TEBD_JACOBI=cluster selects one
   // thread-block cluster per matrix instead
   const char* jv = getenv("PT_TEBD_JACOBI");
@@ -695,8 +718,8 @@ int pt_tebd_init(pt_tebd_t* out, const pt_chain_desc* chains, int n_chains, cons
     return PT_ERR_ARG;
   }
   if (h->opt.max_sweeps <= 0) h->opt.max_sweeps = 60;
-  if (h->opt.precision != PT_FP64) {
-    h->fail(PT_ERR_ARG, "pt_tebd_init: this build supports PT_FP64 only");
+  if (h->opt.precision < PT_FP64 || h->opt.precision > PT_TF32X1) {
+    h->fail(PT_ERR_ARG, "pt_tebd_init: unknown precision");
     delete h;
     return PT_ERR_ARG;
   }

@@ -38,6 +38,12 @@ int jacobi_grid_blocks();
 void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3,
                         int* cnt, int* status, cudaStream_t st);
 
+// tensor-core theta of the fast path (tc_theta.cu); precision: 1 TF32x3, 2 BF16x3, 3 TF32x1
+size_t tc_pack_bytes(int rows_cap, int k_cap, int precision);
+void tc_caps(int rows_cap, int k_cap, int precision, int* rt_cap, int* kc_cap);
+void launch_tc_theta(const Tables& T, const BondWork* work, int n_work, int rt_cap, int kc_cap, int precision,
+                     cudaStream_t st);
+
 // set the message returned by pt_tebd_last_error(NULL) (engine.cu)
 void set_global_error(const char* msg);
 
