@@ -198,6 +198,7 @@ def run_ours(args, rank, world, local):
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    sweeps = eng.get_svd_sweeps()
     total_ms = float(np.sum(step_ms))
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
@@ -239,6 +240,8 @@ def run_ours(args, rank, world, local):
     roofline = {"bound": "alu", "kernel": "k_jacobi (FP64 one-sided Jacobi SVD)",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                 "traffic": None, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x median SM clock",
+                "svd_sweeps_last_step": {"fp64": [int(x) for x in sweeps[:, 0]],
+                                         "fp32": [int(x) for x in sweeps[:, 1]]},
                 "stage_ms_per_step": {"site": stage[0], "blocks_qr": stage[1], "theta": stage[2],
                                       "svd": stage[3], "truncate": stage[4], "recover": stage[5],
                                       "readout": stage[6]}}

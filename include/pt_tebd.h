@@ -126,6 +126,11 @@ int pt_tebd_get_dims(pt_tebd_t h, int chain, int* chi, int* kappa);
 int pt_tebd_get_lambda(pt_tebd_t h, int chain, int bond, double* out, int cap);
 int pt_tebd_get_lognorm(pt_tebd_t h, int chain, double* out);
 
+/* Jacobi sweeps of the most recent update of every bond (odd-layer bonds first, then even):
+ * out[2i] = FP64 sweeps, out[2i+1] = FP32 sweeps (fast path; 0 otherwise); a negative count marks
+ * a bond that hit max_sweeps. Writes min(cap, n_bonds) pairs; returns n_bonds. */
+int pt_tebd_get_svd_sweeps(pt_tebd_t h, int* out, int cap);
+
 /* Copy the whole device state into a new handle (App. B.2: continue from the full augmented MPS). */
 int pt_tebd_clone(pt_tebd_t h, pt_tebd_t* out);
 

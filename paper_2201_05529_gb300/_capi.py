@@ -23,7 +23,8 @@ ERRORS = {-1: "PT_ERR_ARG", -2: "PT_ERR_OOM", -3: "PT_ERR_CAPACITY", -4: "PT_ERR
 EXPORTS = [
     "pt_tebd_set_allocator", "pt_tebd_init", "pt_tebd_set_observables", "pt_tebd_step",
     "pt_tebd_observe", "pt_tebd_read_history", "pt_tebd_apply_local", "pt_tebd_steps_done",
-    "pt_tebd_get_dims", "pt_tebd_get_lambda", "pt_tebd_get_lognorm", "pt_tebd_clone",
+    "pt_tebd_get_dims", "pt_tebd_get_lambda", "pt_tebd_get_lognorm", "pt_tebd_get_svd_sweeps",
+    "pt_tebd_clone",
     "pt_tebd_sync", "pt_tebd_destroy", "pt_tebd_last_error", "pt_tebd_set_timing",
     "pt_tebd_get_timing", "pt_svd_scratch_bytes", "pt_svd_f64", "pt_svd_f64_noalloc",
 ]
@@ -80,6 +81,7 @@ lib.pt_tebd_steps_done.argtypes = [C.c_void_p]
 lib.pt_tebd_get_dims.argtypes = [C.c_void_p, C.c_int, c_int_p, c_int_p]
 lib.pt_tebd_get_lambda.argtypes = [C.c_void_p, C.c_int, C.c_int, c_double_p, C.c_int]
 lib.pt_tebd_get_lognorm.argtypes = [C.c_void_p, C.c_int, c_double_p]
+lib.pt_tebd_get_svd_sweeps.argtypes = [C.c_void_p, c_int_p, C.c_int]
 lib.pt_tebd_clone.argtypes = [C.c_void_p, C.POINTER(C.c_void_p)]
 lib.pt_tebd_sync.argtypes = [C.c_void_p]
 lib.pt_tebd_destroy.argtypes = [C.c_void_p]
@@ -260,6 +262,12 @@ class Engine:
         v = C.c_double()
         _check(lib.pt_tebd_get_lognorm(self.h, int(chain), C.byref(v)), self.h)
         return v.value
+
+    def get_svd_sweeps(self, cap=4096):
+        """[(fp64 sweeps, fp32 sweeps)] of the latest update of every bond (odd layer first)."""
+        out = np.zeros(2 * cap, dtype=np.int32)
+        n = _check(lib.pt_tebd_get_svd_sweeps(self.h, out.ctypes.data_as(c_int_p), cap), self.h)
+        return out[:2 * min(n, cap)].reshape(-1, 2)
 
     def sync(self):
         _check(lib.pt_tebd_sync(self.h), self.h)

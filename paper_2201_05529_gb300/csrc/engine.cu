@@ -80,6 +80,9 @@ struct pt_tebd {
   int cl_odd = 1, cl_even = 1;        // Jacobi cluster sizes per layer list
   int grid_blocks = 0;                // whole-GPU Jacobi: CTAs per launch (0: use the cluster kernel)
   int rt_odd = 1, rt_even = 1, kc_odd = 1, kc_even = 1;   // fast path: theta tile / K-chunk caps
+  std::vector<int*> bond_info;        // per bond (odd list, then even list): its info words
+  bool mixed_svd = true;              // fast path: FP32 bulk sweeps + FP64 polish (PT_TEBD_SVD=fp64 disables)
+  int kcap_odd = 1, kcap_even = 1, mcap_odd = 1, mcap_even = 1;
   unsigned* d_sync3 = nullptr;        // grid barrier state
   int* d_cnt_odd = nullptr;           // per-item rotation counters
   int* d_cnt_even = nullptr;
@@ -214,7 +217,12 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n) {
                          work == h->d_odd ? h->kc_odd : h->kc_even, (int)h->opt.precision, s);
   ev_end(h, e);
   ev_begin(h, 3, &e);
-  if (h->grid_blocks > 0)
+  if (h->grid_blocks > 0 && h->opt.precision != PT_FP64 && h->mixed_svd)
+    ptk::launch_mixed_svd(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3,
+                          work == h->d_odd ? h->d_cnt_odd : h->d_cnt_even, h->T.status,
+                          work == h->d_odd ? h->kcap_odd : h->kcap_even, work == h->d_odd ? h->mcap_odd : h->mcap_even,
+                          std::max(1.1102230246251565e-16, std::min(5.9604644775390625e-8, 0.01 * h->opt.eps)), s);
+  else if (h->grid_blocks > 0)
     ptk::launch_jacobi_grid(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3,
                             work == h->d_odd ? h->d_cnt_odd : h->d_cnt_even, h->T.status, s);
   else
@@ -602,9 +610,15 @@ int build(pt_tebd* h) {
       cudaMemsetAsync(W.info, 0, sizeof(int) * 8, h->stream);
       if (h->opt.precision != PT_FP64) {
         const int kcap = chc;
+        const size_t ma = (size_t)std::max(W.mD_cap, W.nD_cap);
         W.TA = h->dalloc(ptk::tc_pack_bytes(W.mD_cap, kcap, (int)h->opt.precision));
         W.TB = h->dalloc(ptk::tc_pack_bytes(W.nD_cap, kcap, (int)h->opt.precision));
-        if (!W.TA || !W.TB) return h->fail(PT_ERR_OOM, "fast-path operand planes");
+        W.A32 = (float2*)h->dalloc(sizeof(float2) * as);
+        W.V32 = (float2*)h->dalloc(sizeof(float2) * vs);
+        W.G64 = (double2*)h->dalloc(sizeof(double2) * vs);
+        W.Y64 = (double2*)h->dalloc(sizeof(double2) * ma * W.k_cap);
+        if (!W.TA || !W.TB || !W.A32 || !W.V32 || !W.G64 || !W.Y64)
+          return h->fail(PT_ERR_OOM, "fast-path scratch");
       }
       if (W.nL_cap > 2048 || W.mR_cap > 2048)
         return h->fail(PT_ERR_CAPACITY, "QR reduction supports at most 2048 columns (4 chi <= 2048)");
@@ -614,6 +628,8 @@ int build(pt_tebd* h) {
   }
   h->n_odd = (int)odd.size();
   h->n_even = (int)even.size();
+  for (auto& W : odd) h->bond_info.push_back(W.info);
+  for (auto& W : even) h->bond_info.push_back(W.info);
   // cluster size: about 8 column pairs per CTA of 32 warps, at most 16 CTAs per matrix
   auto pick = [&](const std::vector<BondWork>& v) {
     int k = 1;
@@ -633,6 +649,16 @@ int build(pt_tebd* h) {
     };
     caps(odd, &h->rt_odd, &h->kc_odd);
     caps(even, &h->rt_even, &h->kc_even);
+    auto dims = [&](const std::vector<BondWork>& v, int* kc, int* mc) {
+      for (auto& W : v) {
+        *kc = std::max(*kc, W.k_cap);
+        *mc = std::max(*mc, std::max(W.mD_cap, W.nD_cap));
+      }
+    };
+    dims(odd, &h->kcap_odd, &h->mcap_odd);
+    dims(even, &h->kcap_even, &h->mcap_even);
+    const char* sv = getenv("PT_TEBD_SVD");
+    h->mixed_svd = !(sv && std::string(sv) == "fp64");
   }
   // bond SVDs: whole-GPU cooperative kernel by default; PT_TEBD_JACOBI=cluster selects one
   // thread-block cluster per matrix instead
@@ -940,6 +966,20 @@ int pt_tebd_destroy(pt_tebd_t h) {
   h->release();
   delete h;
   return PT_OK;
+}
+
+int pt_tebd_get_svd_sweeps(pt_tebd_t h, int* out, int cap) {
+  if (!h || !out || cap < 0) return PT_ERR_ARG;
+  const int n = std::min(cap, (int)h->bond_info.size());
+  std::vector<int> buf(8);
+  for (int i = 0; i < n; ++i) {
+    cudaMemcpyAsync(buf.data(), h->bond_info[i], sizeof(int) * 8, cudaMemcpyDeviceToHost, h->stream);
+    cudaStreamSynchronize(h->stream);
+    out[2 * i] = buf[3];
+    out[2 * i + 1] = buf[6];
+  }
+  int rc = read_status(h);
+  return rc == PT_OK ? (int)h->bond_info.size() : rc;
 }
 
 int pt_tebd_set_timing(pt_tebd_t h, int enable) {

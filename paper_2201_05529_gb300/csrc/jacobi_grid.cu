@@ -60,71 +60,91 @@ __device__ bool grid_barrier(const GridSync& gs, int* status) {
   return ok_s != 0;
 }
 
-__device__ __forceinline__ double wsumd(double v) {
+template <typename R>
+__device__ __forceinline__ R wsumd(R v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
+template <typename R> struct Cx;
+template <> struct Cx<double> {
+  using T = double2;
+  static constexpr double EPS = 1.1102230246251565e-16;
+  __device__ static T* A(const BondWork& W) { return W.A; }
+  __device__ static T* V(const BondWork& W) { return W.V; }
+};
+template <> struct Cx<float> {
+  using T = float2;
+  static constexpr float EPS = 5.9604644775390625e-8f;
+  __device__ static T* A(const BondWork& W) { return W.A32; }
+  __device__ static T* V(const BondWork& W) { return W.V32; }
+};
+
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-struct ItemDims {
-  double2* A;
-  double2* V;
-  int Ma, Na, Np;
-};
-
-__device__ __forceinline__ ItemDims item_dims(const BondWork& W) {
-  ItemDims d;
+__device__ __forceinline__ void item_shape(const BondWork& W, int* Ma, int* Na) {
   const int mD = W.info[0], nD = W.info[1];
   const bool tr = W.info[2] != 0;
-  d.A = W.A;
-  d.V = W.V;
-  d.Ma = (mD > 0 && nD > 0) ? (tr ? nD : mD) : 0;
-  d.Na = (mD > 0 && nD > 0) ? (tr ? mD : nD) : 0;
-  d.Np = d.Na + (d.Na & 1);
-  return d;
+  *Ma = (mD > 0 && nD > 0) ? (tr ? nD : mD) : 0;
+  *Na = (mD > 0 && nD > 0) ? (tr ? mD : nD) : 0;
 }
 
 }  // namespace
 
-// work: layer items; sync: grid barrier state; cnt: [n_work][2] rotation counters.
-__global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* work, int n_work, int max_sweeps,
-                                                              GridSync gs, int* cnt, int* status) {
+// One-sided Jacobi over all matrices of a layer. R = double: FP64 on W.A / W.V (the FP64 path, and
+// the polishing sweeps of the fast path); R = float: FP32 on W.A32 / W.V32 (the fast path's bulk
+// sweeps). init_v: start from V = I (else from the V already stored). finalize: write sigma, the
+// normalised left vectors and the order. floor_eps: unit roundoff that sets the noise floor.
+// cnt: [n_work][2] rotation counters; sweeps go to info[sweep_slot].
+template <typename R>
+__global__ void __launch_bounds__(GRID_THREADS)
+    k_jacobi_grid(const BondWork* work, int n_work, int max_sweeps, GridSync gs, int* cnt, int* status,
+                  int init_v, int finalize, double floor_eps, int sweep_slot) {
+  using C2 = typename Cx<R>::T;
   __shared__ int s_Na[MAX_ITEMS];
+  __shared__ int s_Ma[MAX_ITEMS];
   __shared__ int s_off[MAX_ITEMS + 1];      // prefix of pair counts of the active items this round
   __shared__ unsigned char s_active[MAX_ITEMS];
-  __shared__ double s_part[GROUPS][GROUP_WARPS][4];
-  __shared__ double s_rot[GROUPS][8];       // rotate flag, c, s, s e^{-i phi}, c e^{-i phi}
-  __shared__ double s_fro[MAX_ITEMS];       // ||A||_F^2 per item (rounding-noise floor)
+  __shared__ C2* s_A[MAX_ITEMS];
+  __shared__ C2* s_V[MAX_ITEMS];
+  __shared__ R s_part[GROUPS][GROUP_WARPS][4];
+  __shared__ R s_rot[GROUPS][8];            // rotate flag, c, s, s e^{-i phi}, c e^{-i phi}
+  __shared__ double s_fro[MAX_ITEMS];       // ||A||_F^2 per item (noise floor)
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int grp = wid / GROUP_WARPS, gw = wid % GROUP_WARPS;
   const int n_groups = gridDim.x * GROUPS;
   const int my_group = grp * gridDim.x + blockIdx.x;     // consecutive tasks go to different SMs
-  const double eps = 1.1102230246251565e-16;
+  const R eps = Cx<R>::EPS;
   if (n_work > MAX_ITEMS) {
     if (blockIdx.x == 0 && tid == 0) atomicOr(status, ST_CAPACITY);
     return;
   }
   for (int w = tid; w < n_work; w += blockDim.x) {
-    const ItemDims d = item_dims(work[w]);
-    s_Na[w] = d.Na;
-    s_active[w] = d.Na >= 2;
+    int Ma, Na;
+    item_shape(work[w], &Ma, &Na);
+    s_Na[w] = Na;
+    s_Ma[w] = Ma;
+    s_active[w] = Na >= 2;
+    s_A[w] = Cx<R>::A(work[w]);
+    s_V[w] = Cx<R>::V(work[w]);
   }
   __syncthreads();
-  // V = I, zero counters, column norms (for the rounding-noise floor)
+  // V = I (optional), zero counters, column norms (for the noise floor)
   {
     const int gt = blockIdx.x * blockDim.x + tid, ngt = gridDim.x * blockDim.x;
     for (int w = 0; w < n_work; ++w) {
       const int Na = s_Na[w];
-      double2* V = work[w].V;
-      for (size_t idx = gt; idx < (size_t)Na * Na; idx += ngt) {
-        double2 v;
-        v.x = ((idx % Na) == (idx / Na)) ? 1.0 : 0.0;
-        v.y = 0.0;
-        __stcg(V + idx, v);
+      if (init_v) {
+        C2* V = s_V[w];
+        for (size_t idx = gt; idx < (size_t)Na * Na; idx += ngt) {
+          C2 v;
+          v.x = ((idx % Na) == (idx / Na)) ? R(1) : R(0);
+          v.y = R(0);
+          __stcg(V + idx, v);
+        }
       }
       if (gt == 0) {
         cnt[2 * w] = 0;
@@ -134,19 +154,19 @@ __global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* wo
     const int gwarp = wid * gridDim.x + blockIdx.x, ngwarp = gridDim.x * (blockDim.x / 32);
     int base = 0;
     for (int w = 0; w < n_work; ++w) {
-      const ItemDims d = item_dims(work[w]);
-      for (int c = gwarp - base; c < d.Na; c += ngwarp) {
+      const int Ma = s_Ma[w], Na = s_Na[w];
+      for (int c = gwarp - base; c < Na; c += ngwarp) {
         if (c < 0) continue;
-        const double2* a = d.A + (size_t)c * d.Ma;
+        const C2* a = s_A[w] + (size_t)c * Ma;
         double s2 = 0;
-        for (int r = lane; r < d.Ma; r += 32) {
-          const double2 x = __ldcg(a + r);
-          s2 += x.x * x.x + x.y * x.y;
+        for (int r = lane; r < Ma; r += 32) {
+          const C2 x = __ldcg(a + r);
+          s2 += (double)x.x * x.x + (double)x.y * x.y;
         }
         s2 = wsumd(s2);
         if (lane == 0) __stcg(work[w].aux + c, s2);
       }
-      base = (base + d.Na) % ngwarp;
+      base = (base + Na) % ngwarp;
     }
   }
   if (!grid_barrier(gs, status)) return;
@@ -165,7 +185,6 @@ __global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* wo
     const int par = sweep & 1;
     if (blockIdx.x == 0)
       for (int w = tid; w < n_work; w += blockDim.x) cnt[2 * w + (par ^ 1)] = 0;
-    // rounds: the longest active tournament sets the count
     int rounds = 0;
     for (int w = 0; w < n_work; ++w)
       if (s_active[w]) rounds = max(rounds, s_Na[w] + (s_Na[w] & 1) - 1);
@@ -182,7 +201,6 @@ __global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* wo
       __syncthreads();
       const int total = s_off[n_work];
       for (int t = my_group; t < total; t += n_groups) {
-        // item of task t (binary search over the offsets)
         int lo = 0, hi = n_work - 1;
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
@@ -191,19 +209,18 @@ __global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* wo
         }
         const int w = lo;
         const int q = t - s_off[w];
-        const ItemDims d = item_dims(work[w]);
-        const int Np = d.Np;
+        const int Ma = s_Ma[w], Na = s_Na[w], Np = Na + (Na & 1);
         int i, j;
         if (q == 0) { i = Np - 1; j = round; }
         else { i = (round + q) % (Np - 1); j = (round - q + Np - 1) % (Np - 1); }
         if (i > j) { const int tt = i; i = j; j = tt; }
-        const bool real_pair = j < d.Na;      // uniform within the group
-        double al = 0, be = 0, gr = 0, gi = 0;
-        double2* ai = d.A + (size_t)i * d.Ma;
-        double2* aj = d.A + (size_t)j * d.Ma;
+        const bool real_pair = j < Na;        // uniform within the group
+        C2* ai = s_A[w] + (size_t)i * Ma;
+        C2* aj = s_A[w] + (size_t)j * Ma;
         if (real_pair) {
-          for (int r = gw * 32 + lane; r < d.Ma; r += 32 * GROUP_WARPS) {
-            const double2 x = __ldcg(ai + r), y = __ldcg(aj + r);
+          R al = 0, be = 0, gr = 0, gi = 0;
+          for (int r = gw * 32 + lane; r < Ma; r += 32 * GROUP_WARPS) {
+            const C2 x = __ldcg(ai + r), y = __ldcg(aj + r);
             al = fma(x.x, x.x, fma(x.y, x.y, al));
             be = fma(y.x, y.x, fma(y.y, y.y, be));
             gr = fma(x.x, y.x, fma(x.y, y.y, gr));
@@ -223,9 +240,9 @@ __global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* wo
         named_sync(1 + grp, 32 * GROUP_WARPS);
         // one lane turns the partial sums (fixed order) into the rotation and shares it
         if (gw == 0 && lane == 0) {
-          double flag = 0.0, c = 1.0, sv = 0.0, ser = 0.0, sei = 0.0, cer = 1.0, cei = 0.0;
+          R flag = 0, c = 1, sv = 0, ser = 0, sei = 0, cer = 1, cei = 0;
           if (real_pair) {
-            al = be = gr = gi = 0;
+            R al = 0, be = 0, gr = 0, gi = 0;
 #pragma unroll
             for (int k = 0; k < GROUP_WARPS; ++k) {
               al += s_part[grp][k][0];
@@ -233,22 +250,24 @@ __global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* wo
               gr += s_part[grp][k][2];
               gi += s_part[grp][k][3];
             }
-            const double g2 = gr * gr + gi * gi;
-            const double tol = (double)d.Ma * eps;
+            const R g2 = gr * gr + gi * gi;
+            const R tol = (R)Ma * eps;
+            const R fl2 = (R)(floor_eps * floor_eps * s_fro[w]);
             // rotate unless |gamma| <= tol sqrt(alpha beta), or a column is at the noise floor
-            // (|a|^2 <= eps^2 ||A||_F^2, see the cluster kernel)
-            if (g2 > tol * tol * al * be && g2 > 0.0 && fmin(al, be) > eps * eps * s_fro[w]) {
-              const double g = sqrt(g2), h = be - al;
+            // (|a|^2 <= floor_eps^2 ||A||_F^2: such columns cannot become orthogonal relative to
+            // their own norm and carry no information at this precision)
+            if (g2 > tol * tol * al * be && g2 > R(0) && fmin(al, be) > fl2) {
+              const R g = sqrt(g2), h = be - al;
               // tan(theta) = 2 g sign(h) / (|h| + sqrt(h^2 + 4 g^2)): the smaller root
-              const double t = (h >= 0.0 ? 2.0 : -2.0) * g / (fabs(h) + sqrt(h * h + 4.0 * g2));
-              c = rsqrt(1.0 + t * t);
+              const R t = (h >= R(0) ? R(2) : R(-2)) * g / (fabs(h) + sqrt(h * h + R(4) * g2));
+              c = R(1) / sqrt(R(1) + t * t);
               sv = c * t;
-              const double sg = sv / g;              // s / |gamma|
-              ser = sg * gr;                          // s e^{-i phi}: e = conj(gamma) / |gamma|
+              const R sg = sv / g;                 // s / |gamma|
+              ser = sg * gr;                        // s e^{-i phi}: e = conj(gamma) / |gamma|
               sei = -sg * gi;
               cer = c * gr / g;
               cei = -c * gi / g;
-              flag = 1.0;
+              flag = 1;
             }
           }
           s_rot[grp][0] = flag;
@@ -260,15 +279,15 @@ __global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* wo
           s_rot[grp][6] = cei;
         }
         named_sync(1 + grp, 32 * GROUP_WARPS);
-        if (!real_pair || s_rot[grp][0] == 0.0) {
+        if (!real_pair || s_rot[grp][0] == R(0)) {
           named_sync(1 + grp, 32 * GROUP_WARPS);
           continue;
         }
-        const double c = s_rot[grp][1], s = s_rot[grp][2], ser = s_rot[grp][3], sei = s_rot[grp][4];
-        const double cer = s_rot[grp][5], cei = s_rot[grp][6];
-        for (int r = gw * 32 + lane; r < d.Ma; r += 32 * GROUP_WARPS) {
-          const double2 x = __ldcg(ai + r), y = __ldcg(aj + r);
-          double2 nx, ny;
+        const R c = s_rot[grp][1], s = s_rot[grp][2], ser = s_rot[grp][3], sei = s_rot[grp][4];
+        const R cer = s_rot[grp][5], cei = s_rot[grp][6];
+        for (int r = gw * 32 + lane; r < Ma; r += 32 * GROUP_WARPS) {
+          const C2 x = __ldcg(ai + r), y = __ldcg(aj + r);
+          C2 nx, ny;
           nx.x = c * x.x - (ser * y.x - sei * y.y);
           nx.y = c * x.y - (ser * y.y + sei * y.x);
           ny.x = s * x.x + (cer * y.x - cei * y.y);
@@ -276,11 +295,11 @@ __global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* wo
           __stcg(ai + r, nx);
           __stcg(aj + r, ny);
         }
-        double2* vi = d.V + (size_t)i * d.Na;
-        double2* vj = d.V + (size_t)j * d.Na;
-        for (int r = gw * 32 + lane; r < d.Na; r += 32 * GROUP_WARPS) {
-          const double2 x = __ldcg(vi + r), y = __ldcg(vj + r);
-          double2 nx, ny;
+        C2* vi = s_V[w] + (size_t)i * Na;
+        C2* vj = s_V[w] + (size_t)j * Na;
+        for (int r = gw * 32 + lane; r < Na; r += 32 * GROUP_WARPS) {
+          const C2 x = __ldcg(vi + r), y = __ldcg(vj + r);
+          C2 nx, ny;
           nx.x = c * x.x - (ser * y.x - sei * y.y);
           nx.y = c * x.y - (ser * y.y + sei * y.x);
           ny.x = s * x.x + (cer * y.x - cei * y.y);
@@ -297,7 +316,7 @@ __global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* wo
       for (int w = 0; w < n_work; ++w)
         if (s_active[w] && *(volatile int*)&cnt[2 * w + par] == 0) {
           s_active[w] = 0;
-          if (blockIdx.x == 0) work[w].info[3] = sweep + 1;
+          if (blockIdx.x == 0) work[w].info[sweep_slot] = sweep + 1;
         }
     __syncthreads();
     any = false;
@@ -308,29 +327,30 @@ __global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* wo
   if (any && blockIdx.x == 0 && tid == 0) {
     atomicOr(status, ST_SVD_NOCONV);
     for (int w = 0; w < n_work; ++w)
-      if (s_active[w]) work[w].info[3] = -sweep;
+      if (s_active[w]) work[w].info[sweep_slot] = -sweep;
   }
+  if (!finalize) return;
   // singular values: column norms, normalise the columns (left vectors), then rank by sigma
   {
     const int gwarp = wid * gridDim.x + blockIdx.x, ngwarp = gridDim.x * (blockDim.x / 32);
     int base = 0;
     for (int w = 0; w < n_work; ++w) {
-      const ItemDims d = item_dims(work[w]);
-      for (int c = gwarp - base; c < d.Na; c += ngwarp) {
+      const int Ma = s_Ma[w], Na = s_Na[w];
+      for (int c = gwarp - base; c < Na; c += ngwarp) {
         if (c < 0) continue;
-        double2* a = d.A + (size_t)c * d.Ma;
-        double s2 = 0;
-        for (int r = lane; r < d.Ma; r += 32) {
-          const double2 x = __ldcg(a + r);
+        C2* a = s_A[w] + (size_t)c * Ma;
+        R s2 = 0;
+        for (int r = lane; r < Ma; r += 32) {
+          const C2 x = __ldcg(a + r);
           s2 += x.x * x.x + x.y * x.y;
         }
         s2 = wsumd(s2);
-        const double sg = sqrt(s2);
-        if (lane == 0) __stcg(work[w].sig + c, sg);
-        if (sg > 0.0) {
-          const double inv = 1.0 / sg;
-          for (int r = lane; r < d.Ma; r += 32) {
-            double2 x = __ldcg(a + r);
+        const R sg = sqrt(s2);
+        if (lane == 0) __stcg(work[w].sig + c, (double)sg);
+        if (sg > R(0)) {
+          const R inv = R(1) / sg;
+          for (int r = lane; r < Ma; r += 32) {
+            C2 x = __ldcg(a + r);
             x.x *= inv;
             x.y *= inv;
             __stcg(a + r, x);
@@ -338,7 +358,7 @@ __global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* wo
         }
         if (lane == 0 && !(sg == sg)) atomicOr(status, ST_NAN);
       }
-      base = (base + d.Na) % ngwarp;
+      base = (base + Na) % ngwarp;
     }
   }
   if (!grid_barrier(gs, status)) return;
@@ -361,15 +381,17 @@ __global__ void __launch_bounds__(GRID_THREADS) k_jacobi_grid(const BondWork* wo
 }
 
 int jacobi_grid_blocks() {
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0, a = 0, b = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_grid, GRID_THREADS, 0);
-  return per_sm >= 1 ? sms : 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_jacobi_grid<double>, GRID_THREADS, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_jacobi_grid<float>, GRID_THREADS, 0);
+  return (a >= 1 && b >= 1) ? sms : 0;
 }
 
 void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3,
-                        int* cnt, int* status, cudaStream_t st) {
+                        int* cnt, int* status, cudaStream_t st, int fp32, int init_v, int finalize,
+                        double floor_eps, int sweep_slot) {
   // barrier arrival count and abort flag start at zero for every launch (the generation never resets)
   cudaMemsetAsync(sync3, 0, sizeof(unsigned), st);
   cudaMemsetAsync(sync3 + 2, 0, sizeof(unsigned), st);
@@ -383,7 +405,12 @@ void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sw
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_jacobi_grid, work, n_work, max_sweeps, gs, cnt, status);
+  if (fp32)
+    cudaLaunchKernelEx(&cfg, k_jacobi_grid<float>, work, n_work, max_sweeps, gs, cnt, status, init_v, finalize,
+                       floor_eps, sweep_slot);
+  else
+    cudaLaunchKernelEx(&cfg, k_jacobi_grid<double>, work, n_work, max_sweeps, gs, cnt, status, init_v, finalize,
+                       floor_eps, sweep_slot);
 }
 
 }  // namespace ptk

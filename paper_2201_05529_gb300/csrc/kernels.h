@@ -35,8 +35,15 @@ void launch_jacobi_cluster(const BondWork* work, int n_work, int cluster, int ma
 // whole-GPU FP64 bond SVD (jacobi_grid.cu): blocks = one per SM (0 if not co-schedulable);
 // sync3: 3 words of device memory (arrival count, generation, abort flag); cnt: 2 ints per item
 int jacobi_grid_blocks();
+// fp32: sweeps in FP32 on A32/V32; init_v: start from V = I; finalize: sigma, U, order;
+// floor_eps: unit roundoff of the noise floor; sweep_slot: info[] index for the sweep count
 void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3,
-                        int* cnt, int* status, cudaStream_t st);
+                        int* cnt, int* status, cudaStream_t st, int fp32 = 0, int init_v = 1, int finalize = 1,
+                        double floor_eps = 1.1102230246251565e-16, int sweep_slot = 3);
+
+// fast path: FP32 bulk sweeps + FP64 Newton-Schulz re-orthonormalisation + FP64 polish (mixed_svd.cu)
+void launch_mixed_svd(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,
+                      int* status, int k_cap, int m_cap, double polish_floor, cudaStream_t st);
 
 // tensor-core theta of the fast path (tc_theta.cu); precision: 1 TF32x3, 2 BF16x3, 3 TF32x1
 size_t tc_pack_bytes(int rows_cap, int k_cap, int precision);
