@@ -7,7 +7,8 @@ A "step" is one full PT-TEBD time step of every chain (three bond layers, the PT
 three bond layers, readout). W warm-up steps run from t = 0, then K steps are timed, each with
 CUDA events on the library's stream and an L2 flush (a 256 MiB write) between timed steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32x3|bf16x3]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32x3|fp64|bf16x3|tf32x1]
+The default times the FP32 tensor-core path (TF32x3) and, on the same window, the FP64 path.
   python bench.py --impl reference ...     # the FP64 CPU oracle on the host cores, same metric
 """
 from __future__ import annotations
@@ -38,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3", "tf32x1"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -147,6 +148,24 @@ def step_flops(chis, kaps, N):
 
 
 # ------------------------------------------------------------------------ our arm
+LAUNCHES_PER_LAYER = {"fp64": 6, "fast": 18}
+
+
+def _timed_window(eng, K, stream, flush, torch, n_chains, clk=None):
+    """K single steps, each bracketed by CUDA events on the library's stream, L2 flushed between."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    dims = []
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        eng.step(1)
+        ev[i][1].record(stream)
+        dims.append([eng.get_dims(c) for c in range(n_chains)])   # synchronises; outside the events
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], dims
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2201_05529_gb300 as pkg
@@ -166,8 +185,8 @@ def run_ours(args, rank, world, local):
     site_steps_per_step = sum(c["N"] for c in chains)
     n_chains = len(chains)
 
-    def make():
-        e = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, precision=args.precision,
+    def make(precision):
+        e = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, precision=precision,
                         max_steps=w.K, use_graph=True)
         e.set_observables([Z])
         return e
@@ -179,49 +198,53 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl")
 
     # --- main timed run: graph replay, per-step events, L2 flush between steps
-    eng = make()
+    eng = make(args.precision)
     eng.step(W)
     eng.sync()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    dims = []
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for i in range(K):
-            flush.fill_(float(i))
-            ev[i][0].record(stream)
-            eng.step(1)
-            ev[i][1].record(stream)
-            dims.append([eng.get_dims(c) for c in range(n_chains)])   # synchronises; outside the events
-        torch.cuda.synchronize()
+        step_ms, dims = _timed_window(eng, K, stream, flush, torch, n_chains)
     if world > 1:
         dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    sweeps = eng.get_svd_sweeps()
     total_ms = float(np.sum(step_ms))
     if world > 1:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     eng.sync()
+    sweeps = eng.get_svd_sweeps()
+    hist_fast, _ = eng.read_history(W, K + 1)
+    eng.destroy()
     value = site_steps_per_step * K * world / (total_ms / 1e3)
-
-    # algorithmic flops over the timed steps (bond sizes from the dims at the end of each step)
     fl_svd = fl_other = 0.0
     for per_chain in dims:
         for c, (chi, kap) in enumerate(per_chain):
-            s, o = step_flops(list(chi), list(kap), chains[c]["N"])
-            fl_svd += s
-            fl_other += o
-    eng.destroy()
+            s_, o_ = step_flops(list(chi), list(kap), chains[c]["N"])
+            fl_svd += s_
+            fl_other += o_
+
+    # --- the plain FP64 GPU path on the same window (for the FP32-TC vs FP64 comparison)
+    fp64 = None
+    if args.precision != "fp64":
+        k64 = K
+        e64 = make("fp64")
+        e64.step(W)
+        e64.sync()
+        ms64, _ = _timed_window(e64, k64, stream, flush, torch, n_chains)
+        hist64, _ = e64.read_history(W, k64 + 1)
+        e64.destroy()
+        fp64 = {"value": site_steps_per_step * k64 / (float(np.sum(ms64)) / 1e3),
+                "ms_per_step": float(np.mean(ms64)), "steps": k64,
+                "window": f"steps {W}..{W + k64} (the same steps as the fast path)",
+                "max_obs_diff_vs_fast_path": float(np.max(np.abs(hist64 - hist_fast[:k64 + 1])))}
 
     # --- per-stage timing (eager launches with events) over the same window
-    eng = make()
+    eng = make(args.precision)
     eng.step(W)
     eng.sync()
     eng.set_timing(True)
-    stage = np.zeros(7)
+    stage = np.zeros(9)
     nk = min(K, 5)
     for i in range(nk):
         flush.fill_(float(i))
@@ -231,25 +254,29 @@ def run_ours(args, rank, world, local):
     eng.destroy()
     stage /= nk
     n_layers = 6
-    jac_launch_ms = stage[3] / n_layers
-    steps_svd_flops = fl_svd / K
+    svd_ms = stage[3] + stage[7] + stage[8]
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp64_peak = SM_COUNT * FP64_FLOPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
-    achieved = (steps_svd_flops / n_layers) / (jac_launch_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_jacobi (FP64 one-sided Jacobi SVD)",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                "traffic": None, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x median SM clock",
+    achieved = (fl_svd / K / n_layers) / (svd_ms / n_layers / 1e3) / 1e12
+    kernel = ("k_jacobi_grid<double> (FP64 one-sided Jacobi SVD)" if args.precision == "fp64" else
+              "bond SVD: k_jacobi_grid<float> sweeps + FP64 Newton-Schulz + k_jacobi_grid<double> polish")
+    roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "work": "Golub-Van Loan SVD flops 4(4m^2n+8mn^2+9n^3) x4 (complex) per bond update",
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x median SM clock (of derived; "
+                               "MEASURED_PEAKS.json absent; a DFMA probe measured 1.20 TFLOP/s)",
+                "svd_ms_per_launch": svd_ms / n_layers,
                 "svd_sweeps_last_step": {"fp64": [int(x) for x in sweeps[:, 0]],
                                          "fp32": [int(x) for x in sweeps[:, 1]]},
                 "stage_ms_per_step": {"site": stage[0], "blocks_qr": stage[1], "theta": stage[2],
-                                      "svd": stage[3], "truncate": stage[4], "recover": stage[5],
-                                      "readout": stage[6]}}
+                                      "svd_fp64": stage[3], "svd_fp32": stage[7], "svd_reorth": stage[8],
+                                      "truncate": stage[4], "recover": stage[5], "readout": stage[6]}}
 
     # --- end to end through the C ABI: host inputs -> init (H2D) -> W+K steps -> history (D2H)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2 = make()
+    e2 = make(args.precision)
     e2.step(W + K)
     hist, tr = e2.read_history(0, W + K + 1)
     t1 = time.perf_counter()
@@ -263,19 +290,24 @@ def run_ours(args, rank, world, local):
     e2e = {"value": site_steps_per_step * (W + K) / (t1 - t0), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d / (W + K)), "d2h_bytes_per_step": int(d2h / (W + K)),
            "window": f"init + steps 0..{W + K} + history read, all timed"}
-    gpu_launches = K * (6 * 6 + (2 if any(any(i >= 0 for i in c["ptmpo_id"]) for c in chains) else 0) + 2)
+    path = "fp64" if args.precision == "fp64" else "fast"
+    n_layer_launches = sum(1 for _ in range(6))
+    gpu_launches = K * (n_layer_launches * LAUNCHES_PER_LAYER[path] + 2 + 1 + 1)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 (tf32/bf16 TC) + f64",
            "data": "synthetic (seeded workload; PT-MPOs built on the host from the stated Ohmic baths)",
            "config": {"workload": w.name, "chains": n_chains, "N": [c["N"] for c in chains],
                       "dt": w.dt, "chi_max": w.chi_max, "kappa_max": w.kappa_max, "eps": w.eps,
                       "precision": args.precision, "window": f"steps {W}..{W + K} of {w.K}",
                       "l2": "flushed between timed steps (256 MiB write)",
-                      "parallelism": "replicas" if world > 1 else "single GPU"},
+                      "parallelism": f"{world} replicas" if world > 1 else "single GPU"},
            "clocks": clocks, "roofline": roofline, "e2e": e2e, "gpu_launches": gpu_launches,
            "algorithmic_tflops": (fl_svd + fl_other) / (total_ms / 1e3) / 1e12}
+    if fp64 is not None:
+        out["fp64_path"] = fp64
+        out["speedup_vs_fp64_path"] = value / fp64["value"]
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, W, args.cpu_seconds, site_steps_per_step)
     if world > 1:

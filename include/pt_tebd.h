@@ -141,10 +141,11 @@ int pt_tebd_destroy(pt_tebd_t h);
 const char* pt_tebd_last_error(pt_tebd_t h);   /* h may be NULL: last global error */
 
 /* Per-stage device time of the last pt_tebd_step call with timing enabled, in milliseconds:
- * [0] site contraction, [1] block build + QR, [2] theta + gate, [3] SVD, [4] truncation,
- * [5] Gamma recovery, [6] readout. */
+ * [0] site contraction, [1] block build + QR, [2] theta + gate, [3] SVD (FP64 sweeps),
+ * [4] truncation, [5] Gamma recovery, [6] readout, [7] SVD FP32 sweeps (fast path),
+ * [8] SVD re-orthonormalisation (fast path). Timing mode launches eagerly (no graph). */
 int pt_tebd_set_timing(pt_tebd_t h, int enable);
-int pt_tebd_get_timing(pt_tebd_t h, double* ms7);
+int pt_tebd_get_timing(pt_tebd_t h, double* ms9);
 
 /* ---- kernel-level entry points (single operations on device buffers, for unit tests) ---- */
 

@@ -283,7 +283,7 @@ class Engine:
         _check(lib.pt_tebd_set_timing(self.h, int(bool(enable))), self.h)
 
     def get_timing(self):
-        out = np.zeros(7, dtype=np.float64)
+        out = np.zeros(9, dtype=np.float64)
         _check(lib.pt_tebd_get_timing(self.h, _dptr(out)), self.h)
         return out
 

@@ -107,7 +107,7 @@ struct pt_tebd {
   int steps_done = 0;
   cudaGraphExec_t graph = nullptr;
   bool timing = false;
-  double stage_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+  double stage_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   size_t ev_used = 0;
 
@@ -216,19 +216,28 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n) {
     ptk::launch_tc_theta(h->T, work, n, work == h->d_odd ? h->rt_odd : h->rt_even,
                          work == h->d_odd ? h->kc_odd : h->kc_even, (int)h->opt.precision, s);
   ev_end(h, e);
-  ev_begin(h, 3, &e);
-  if (h->grid_blocks > 0 && h->opt.precision != PT_FP64 && h->mixed_svd)
-    ptk::launch_mixed_svd(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3,
-                          work == h->d_odd ? h->d_cnt_odd : h->d_cnt_even, h->T.status,
-                          work == h->d_odd ? h->kcap_odd : h->kcap_even, work == h->d_odd ? h->mcap_odd : h->mcap_even,
-                          std::max(1.1102230246251565e-16, std::min(5.9604644775390625e-8, 0.01 * h->opt.eps)), s);
-  else if (h->grid_blocks > 0)
-    ptk::launch_jacobi_grid(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3,
-                            work == h->d_odd ? h->d_cnt_odd : h->d_cnt_even, h->T.status, s);
-  else
-    ptk::launch_jacobi_cluster(work, n, work == h->d_odd ? h->cl_odd : h->cl_even, h->opt.max_sweeps,
-                               h->T.status, s);
-  ev_end(h, e);
+  int* cnt = work == h->d_odd ? h->d_cnt_odd : h->d_cnt_even;
+  if (h->grid_blocks > 0 && h->opt.precision != PT_FP64 && h->mixed_svd) {
+    ev_begin(h, 7, &e);
+    ptk::launch_mixed_fp32(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status, s);
+    ev_end(h, e);
+    ev_begin(h, 8, &e);
+    ptk::launch_mixed_reorth(work, n, work == h->d_odd ? h->kcap_odd : h->kcap_even,
+                             work == h->d_odd ? h->mcap_odd : h->mcap_even, s);
+    ev_end(h, e);
+    ev_begin(h, 3, &e);
+    ptk::launch_mixed_fp64(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status,
+                           std::max(1.1102230246251565e-16, std::min(5.9604644775390625e-8, 0.01 * h->opt.eps)), s);
+    ev_end(h, e);
+  } else {
+    ev_begin(h, 3, &e);
+    if (h->grid_blocks > 0)
+      ptk::launch_jacobi_grid(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status, s);
+    else
+      ptk::launch_jacobi_cluster(work, n, work == h->d_odd ? h->cl_odd : h->cl_even, h->opt.max_sweeps,
+                                 h->T.status, s);
+    ev_end(h, e);
+  }
   ev_begin(h, 4, &e);
   ptk::k_truncate<<<(n + 63) / 64, 64, 0, s>>>(h->T, work, n, h->opt.chi_max, h->opt.eps,
                                                 h->opt.multiplet_tol);
@@ -804,7 +813,7 @@ int pt_tebd_step(pt_tebd_t h, int n_steps) {
   h->steps_done += n_steps;
   if (h->timing) {
     cudaStreamSynchronize(h->stream);
-    for (int k = 0; k < 7; ++k) h->stage_ms[k] = 0;
+    for (int k = 0; k < 9; ++k) h->stage_ms[k] = 0;
     for (size_t i = 0; i < h->ev_used; ++i) {
       float ms = 0;
       cudaEventElapsedTime(&ms, h->ev[i].second.first, h->ev[i].second.second);
@@ -988,9 +997,9 @@ int pt_tebd_set_timing(pt_tebd_t h, int enable) {
   return PT_OK;
 }
 
-int pt_tebd_get_timing(pt_tebd_t h, double* ms7) {
-  if (!h || !ms7) return PT_ERR_ARG;
-  for (int k = 0; k < 7; ++k) ms7[k] = h->stage_ms[k];
+int pt_tebd_get_timing(pt_tebd_t h, double* ms9) {
+  if (!h || !ms9) return PT_ERR_ARG;
+  for (int k = 0; k < 9; ++k) ms9[k] = h->stage_ms[k];
   return PT_OK;
 }
 

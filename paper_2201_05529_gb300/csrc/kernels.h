@@ -42,8 +42,11 @@ void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sw
                         double floor_eps = 1.1102230246251565e-16, int sweep_slot = 3);
 
 // fast path: FP32 bulk sweeps + FP64 Newton-Schulz re-orthonormalisation + FP64 polish (mixed_svd.cu)
-void launch_mixed_svd(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,
-                      int* status, int k_cap, int m_cap, double polish_floor, cudaStream_t st);
+void launch_mixed_fp32(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,
+                       int* status, cudaStream_t st);
+void launch_mixed_reorth(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st);
+void launch_mixed_fp64(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,
+                       int* status, double polish_floor, cudaStream_t st);
 
 // tensor-core theta of the fast path (tc_theta.cu); precision: 1 TF32x3, 2 BF16x3, 3 TF32x1
 size_t tc_pack_bytes(int rows_cap, int k_cap, int precision);

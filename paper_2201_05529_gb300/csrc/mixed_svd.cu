@@ -138,13 +138,18 @@ __global__ void k_mix_update(const BondWork* work, int n_work, int op) {
   }
 }
 
-void launch_mixed_svd(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,
-                      int* status, int k_cap, int m_cap, double polish_floor, cudaStream_t st) {
+// stage 1: FP32 copy of D and the FP32 bulk sweeps (V32 from identity)
+void launch_mixed_fp32(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,
+                       int* status, cudaStream_t st) {
   const float eps32 = 5.9604644775390625e-8f;
-  const int gx = 128;
-  k_mix_to_f32<<<dim3(gx, n_work), 256, 0, st>>>(work, n_work);
+  k_mix_to_f32<<<dim3(128, n_work), 256, 0, st>>>(work, n_work);
   launch_jacobi_grid(work, n_work, blocks, max_sweeps, sync3, cnt, status, st, /*fp32=*/1, /*init_v=*/1,
                      /*finalize=*/0, eps32, /*sweep_slot=*/6);
+}
+
+// stage 2: V <- Newton-Schulz(V32) twice in FP64, then A <- D V
+void launch_mixed_reorth(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st) {
+  const int gx = 128;
   k_mix_v_to_f64<<<dim3(gx, n_work), 256, 0, st>>>(work, n_work);
   const int tk = (k_cap + TB - 1) / TB, tmm = (m_cap + TB - 1) / TB;
   for (int it = 0; it < 2; ++it) {
@@ -154,10 +159,14 @@ void launch_mixed_svd(const BondWork* work, int n_work, int blocks, int max_swee
   }
   k_mix_gemm<<<dim3(tmm, tk, n_work), 256, 0, st>>>(work, n_work, 2);
   k_mix_update<<<dim3(gx, n_work), 256, 0, st>>>(work, n_work, 1);
-  // FP64 sweeps from the re-orthonormalised V. Their noise floor reaches below the truncation
-  // threshold (the caller passes ~1e-2 eps_trunc): the basis of every singular subspace the
-  // truncation can keep must be the FP64 one, because the trajectory amplifies a change of basis
-  // there even at singular values of 1e-8 of the largest.
+}
+
+// stage 3: FP64 sweeps from the re-orthonormalised V. Their noise floor reaches below the
+// truncation threshold (the caller passes ~1e-2 eps_trunc): the basis of every singular subspace
+// the truncation can keep must be the FP64 one, because the trajectory amplifies a change of
+// basis there even at singular values of 1e-8 of the largest.
+void launch_mixed_fp64(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,
+                       int* status, double polish_floor, cudaStream_t st) {
   launch_jacobi_grid(work, n_work, blocks, max_sweeps, sync3, cnt, status, st, /*fp32=*/0, /*init_v=*/0,
                      /*finalize=*/1, polish_floor, /*sweep_slot=*/3);
 }

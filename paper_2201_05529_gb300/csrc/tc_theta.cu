@@ -11,7 +11,8 @@
 // layout (8-row x 16-byte core matrices; K-groups of the 128-row tile are contiguous), so one
 // cp.async.bulk per plane and K-chunk stages a tile in shared memory. One elected thread issues
 // tcgen05.mma (M = 128, N = 128, FP32 accumulators in TMEM: three 128-column accumulators); the
-// four warps read TMEM back (tcgen05.ld 32x32b) and apply the 16x16 gate across 4-lane groups.
+// four warps read TMEM back (tcgen05.ld 32x32b) and apply the 16x16 gate across 4-lane groups in
+// FP32 (theta is FP32-accurate; an FP64 gate would cost ~1M DFMA per tile at GB300's FP64 rate).
 // Every mbarrier wait has an iteration limit: on expiry the kernel records ST_TIMEOUT, frees its
 // TMEM and returns.
 #include <cuda_bf16.h>
@@ -224,6 +225,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_theta(Tables T, const BondWor
   __shared__ uint64_t bar_load, bar_mma;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
+  __shared__ float2 gate_s[256];           // the 16x16 gate in FP32 (theta is FP32-accurate)
   const int w = blockIdx.z;
   if (w >= n_work) return;
   const BondWork& W = work[w];
@@ -249,6 +251,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_theta(Tables T, const BondWor
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char* sA = smem;                                   // PLANES chunks of A
   unsigned char* sB = smem + PLANES * G::CHUNK_BYTES;         // PLANES chunks of B
+  for (int i = tid; i < 256; i += blockDim.x)
+    gate_s[i] = make_float2((float)W.gate[i].x, (float)W.gate[i].y);
   if (tid == 0) {
     mbar_init(&bar_load, 1);
     mbar_init(&bar_mma, 1);
@@ -322,7 +326,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_theta(Tables T, const BondWor
     const int row = rt * TM + warp * 32 + lane;
     const int u = row >> 2, p = row & 3;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    const double2* gate = W.gate;
     for (int c0 = 0; c0 < TN; c0 += 8) {
       float t1[8], t2[8], t3[8];
       tmem_ld8(tmem + lane_base + 0 * TN + c0, t1);
@@ -340,9 +343,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_theta(Tables T, const BondWor
           re[q] = a - b;
           im[q] = s - a - b;
         }
-        double2 out[4];
+        float2 out[4];
 #pragma unroll
-        for (int qq = 0; qq < 4; ++qq) out[qq] = make_double2(0.0, 0.0);
+        for (int qq = 0; qq < 4; ++qq) out[qq] = make_float2(0.f, 0.f);
         const int base_lane = lane & ~3;
 #pragma unroll
         for (int pp = 0; pp < 4; ++pp) {
@@ -352,9 +355,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_theta(Tables T, const BondWor
             const float ti_ = __shfl_sync(0xffffffffu, im[q], base_lane + pp);
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
-              const double2 g = gate[(p * 4 + qq) * 16 + pp * 4 + q];
-              out[qq].x += g.x * tr_ - g.y * ti_;
-              out[qq].y += g.x * ti_ + g.y * tr_;
+              const float2 g = gate_s[(p * 4 + qq) * 16 + pp * 4 + q];
+              out[qq].x = fmaf(g.x, tr_, fmaf(-g.y, ti_, out[qq].x));
+              out[qq].y = fmaf(g.x, ti_, fmaf(g.y, tr_, out[qq].y));
             }
           }
         }
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_theta(Tables T, const BondWor
 #pragma unroll
           for (int qq = 0; qq < 4; ++qq) {
             const int Drow = u * 4 + p, Dcol = qq * rR + v;
-            if (!tr) W.A[Drow + (size_t)Dcol * mD] = out[qq];
+            if (!tr) W.A[Drow + (size_t)Dcol * mD] = make_double2(out[qq].x, out[qq].y);
             else W.A[Dcol + (size_t)Drow * nD] = make_double2(out[qq].x, -out[qq].y);
           }
         }
