@@ -94,6 +94,113 @@ __device__ __forceinline__ void item_shape(const BondWork& W, int* Ma, int* Na) 
 
 }  // namespace
 
+// One column pair (i, j) of matrix w, processed by the 4 warps of group grp (rows split across
+// them). Returns nothing; counts a rotation in cnt. Every warp of the group must call it.
+template <typename R>
+__device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R>::T* V, int Ma, int Na, int i,
+                                             int j, double fro, double floor_eps, int grp, int gw, int lane,
+                                             R (*s_part)[GROUP_WARPS][4], R (*s_rot)[8], int* cnt_slot) {
+  using C2 = typename Cx<R>::T;
+  const R eps = Cx<R>::EPS;
+  if (i > j) { const int tt = i; i = j; j = tt; }
+  const bool real_pair = j < Na;        // uniform within the group
+  if (!real_pair) return;
+  C2* ai = A + (size_t)i * Ma;
+  C2* aj = A + (size_t)j * Ma;
+  C2* vi = V + (size_t)i * Na;
+  C2* vj = V + (size_t)j * Na;
+  const int r0 = gw * 32 + lane;
+  {
+    R al = 0, be = 0, gr = 0, gi = 0;
+    for (int r = r0; r < Ma; r += 32 * GROUP_WARPS) {
+      const C2 x = __ldcg(ai + r), y = __ldcg(aj + r);
+      al = fma(x.x, x.x, fma(x.y, x.y, al));
+      be = fma(y.x, y.x, fma(y.y, y.y, be));
+      gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+      gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+    }
+    al = wsumd(al);
+    be = wsumd(be);
+    gr = wsumd(gr);
+    gi = wsumd(gi);
+    if (lane == 0) {
+      s_part[grp][gw][0] = al;
+      s_part[grp][gw][1] = be;
+      s_part[grp][gw][2] = gr;
+      s_part[grp][gw][3] = gi;
+    }
+  }
+  named_sync(1 + grp, 32 * GROUP_WARPS);
+  // one lane turns the partial sums (fixed order) into the rotation and shares it
+  if (gw == 0 && lane == 0) {
+    R flag = 0, c = 1, sv = 0, ser = 0, sei = 0, cer = 1, cei = 0;
+    if (real_pair) {
+      R al = 0, be = 0, gr = 0, gi = 0;
+#pragma unroll
+      for (int k = 0; k < GROUP_WARPS; ++k) {
+        al += s_part[grp][k][0];
+        be += s_part[grp][k][1];
+        gr += s_part[grp][k][2];
+        gi += s_part[grp][k][3];
+      }
+      const R g2 = gr * gr + gi * gi;
+      const R tol = (R)Ma * eps;
+      const R fl2 = (R)(floor_eps * floor_eps * fro);
+      // rotate unless |gamma| <= tol sqrt(alpha beta), or a column is at the noise floor
+      // (|a|^2 <= floor_eps^2 ||A||_F^2: such columns cannot become orthogonal relative to
+      // their own norm and carry no information at this precision)
+      if (g2 > tol * tol * al * be && g2 > R(0) && fmin(al, be) > fl2) {
+        const R g = sqrt(g2), h = be - al;
+        // tan(theta) = 2 g sign(h) / (|h| + sqrt(h^2 + 4 g^2)): the smaller root
+        const R t = (h >= R(0) ? R(2) : R(-2)) * g / (fabs(h) + sqrt(h * h + R(4) * g2));
+        c = R(1) / sqrt(R(1) + t * t);
+        sv = c * t;
+        const R sg = sv / g;                 // s / |gamma|
+        ser = sg * gr;                        // s e^{-i phi}: e = conj(gamma) / |gamma|
+        sei = -sg * gi;
+        cer = c * gr / g;
+        cei = -c * gi / g;
+        flag = 1;
+      }
+    }
+    s_rot[grp][0] = flag;
+    s_rot[grp][1] = c;
+    s_rot[grp][2] = sv;
+    s_rot[grp][3] = ser;
+    s_rot[grp][4] = sei;
+    s_rot[grp][5] = cer;
+    s_rot[grp][6] = cei;
+  }
+  named_sync(1 + grp, 32 * GROUP_WARPS);
+  if (!real_pair || s_rot[grp][0] == R(0)) {
+    named_sync(1 + grp, 32 * GROUP_WARPS);
+    return;
+  }
+  const R c = s_rot[grp][1], s = s_rot[grp][2], ser = s_rot[grp][3], sei = s_rot[grp][4];
+  const R cer = s_rot[grp][5], cei = s_rot[grp][6];
+  for (int r = r0; r < Ma; r += 32 * GROUP_WARPS) {
+    const C2 x = __ldcg(ai + r), y = __ldcg(aj + r);
+    C2 nx, ny;
+    nx.x = c * x.x - (ser * y.x - sei * y.y);
+    nx.y = c * x.y - (ser * y.y + sei * y.x);
+    ny.x = s * x.x + (cer * y.x - cei * y.y);
+    ny.y = s * x.y + (cer * y.y + cei * y.x);
+    __stcg(ai + r, nx);
+    __stcg(aj + r, ny);
+  }
+  for (int r = r0; r < Na; r += 32 * GROUP_WARPS) {
+    const C2 x = __ldcg(vi + r), y = __ldcg(vj + r);
+    C2 nx, ny;
+    nx.x = c * x.x - (ser * y.x - sei * y.y);
+    nx.y = c * x.y - (ser * y.y + sei * y.x);
+    ny.x = s * x.x + (cer * y.x - cei * y.y);
+    ny.y = s * x.y + (cer * y.y + cei * y.x);
+    __stcg(vi + r, nx);
+    __stcg(vj + r, ny);
+  }
+  if (gw == 0 && lane == 0) atomicAdd(cnt_slot, 1);
+}
+
 // One-sided Jacobi over all matrices of a layer. R = double: FP64 on W.A / W.V (the FP64 path, and
 // the polishing sweeps of the fast path); R = float: FP32 on W.A32 / W.V32 (the fast path's bulk
 // sweeps). init_v: start from V = I (else from the V already stored). finalize: write sigma, the
@@ -115,8 +222,9 @@ __global__ void __launch_bounds__(GRID_THREADS)
   __shared__ double s_fro[MAX_ITEMS];       // ||A||_F^2 per item (noise floor)
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int grp = wid / GROUP_WARPS, gw = wid % GROUP_WARPS;
-  const int n_groups = gridDim.x * GROUPS;
-  const int my_group = grp * gridDim.x + blockIdx.x;     // consecutive tasks go to different SMs
+  const int slot = grp / 2, sub = grp % 2;               // a task slot = 2 groups = 8 warps
+  const int n_slots = gridDim.x * (GROUPS / 2);
+  const int my_slot = slot * gridDim.x + blockIdx.x;     // consecutive tasks go to different SMs
   const R eps = Cx<R>::EPS;
   if (n_work > MAX_ITEMS) {
     if (blockIdx.x == 0 && tid == 0) atomicOr(status, ST_CAPACITY);
@@ -185,22 +293,28 @@ __global__ void __launch_bounds__(GRID_THREADS)
     const int par = sweep & 1;
     if (blockIdx.x == 0)
       for (int w = tid; w < n_work; w += blockDim.x) cnt[2 * w + (par ^ 1)] = 0;
+    // 2-column blocks: a task pairs two blocks and runs their cross pairs (and, in round 0, the
+    // pairs inside each block) in sub-rounds separated by a barrier of the task's 8 warps; the
+    // round-robin tournament runs over blocks, so a sweep has half as many grid barriers
     int rounds = 0;
     for (int w = 0; w < n_work; ++w)
-      if (s_active[w]) rounds = max(rounds, s_Na[w] + (s_Na[w] & 1) - 1);
+      if (s_active[w]) {
+        const int nb = (s_Na[w] + 1) / 2, nbp = nb + (nb & 1);
+        rounds = max(rounds, nbp - 1);
+      }
     for (int round = 0; round < rounds; ++round) {
       if (tid == 0) {
         int o = 0;
         for (int w = 0; w < n_work; ++w) {
           s_off[w] = o;
-          const int Np = s_Na[w] + (s_Na[w] & 1);
-          if (s_active[w] && round < Np - 1) o += Np / 2;
+          const int nb = (s_Na[w] + 1) / 2, nbp = nb + (nb & 1);
+          if (s_active[w] && round < nbp - 1) o += nbp / 2;
         }
         s_off[n_work] = o;
       }
       __syncthreads();
       const int total = s_off[n_work];
-      for (int t = my_group; t < total; t += n_groups) {
+      for (int t = my_slot; t < total; t += n_slots) {
         int lo = 0, hi = n_work - 1;
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
@@ -209,105 +323,22 @@ __global__ void __launch_bounds__(GRID_THREADS)
         }
         const int w = lo;
         const int q = t - s_off[w];
-        const int Ma = s_Ma[w], Na = s_Na[w], Np = Na + (Na & 1);
-        int i, j;
-        if (q == 0) { i = Np - 1; j = round; }
-        else { i = (round + q) % (Np - 1); j = (round - q + Np - 1) % (Np - 1); }
-        if (i > j) { const int tt = i; i = j; j = tt; }
-        const bool real_pair = j < Na;        // uniform within the group
-        C2* ai = s_A[w] + (size_t)i * Ma;
-        C2* aj = s_A[w] + (size_t)j * Ma;
-        if (real_pair) {
-          R al = 0, be = 0, gr = 0, gi = 0;
-          for (int r = gw * 32 + lane; r < Ma; r += 32 * GROUP_WARPS) {
-            const C2 x = __ldcg(ai + r), y = __ldcg(aj + r);
-            al = fma(x.x, x.x, fma(x.y, x.y, al));
-            be = fma(y.x, y.x, fma(y.y, y.y, be));
-            gr = fma(x.x, y.x, fma(x.y, y.y, gr));
-            gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
-          }
-          al = wsumd(al);
-          be = wsumd(be);
-          gr = wsumd(gr);
-          gi = wsumd(gi);
-          if (lane == 0) {
-            s_part[grp][gw][0] = al;
-            s_part[grp][gw][1] = be;
-            s_part[grp][gw][2] = gr;
-            s_part[grp][gw][3] = gi;
-          }
+        const int Ma = s_Ma[w], Na = s_Na[w];
+        const int nb = (Na + 1) / 2, nbp = nb + (nb & 1);
+        int bi, bj;
+        if (q == 0) { bi = nbp - 1; bj = round; }
+        else { bi = (round + q) % (nbp - 1); bj = (round - q + nbp - 1) % (nbp - 1); }
+        const int i0 = 2 * bi, j0 = 2 * bj;
+        const int n_sub = round == 0 ? 3 : 2;
+        for (int sr = 0; sr < n_sub; ++sr) {
+          int i, j;
+          if (sr == 0) { i = i0 + sub; j = j0 + sub; }
+          else if (sr == 1) { i = i0 + sub; j = j0 + 1 - sub; }
+          else { i = sub == 0 ? i0 : j0; j = i + 1; }          // pairs inside each block
+          process_pair<R>(s_A[w], s_V[w], Ma, Na, i, j, s_fro[w], floor_eps, grp, gw, lane, s_part, s_rot,
+                          &cnt[2 * w + par]);
+          named_sync(9 + slot, 32 * GROUP_WARPS * 2);
         }
-        named_sync(1 + grp, 32 * GROUP_WARPS);
-        // one lane turns the partial sums (fixed order) into the rotation and shares it
-        if (gw == 0 && lane == 0) {
-          R flag = 0, c = 1, sv = 0, ser = 0, sei = 0, cer = 1, cei = 0;
-          if (real_pair) {
-            R al = 0, be = 0, gr = 0, gi = 0;
-#pragma unroll
-            for (int k = 0; k < GROUP_WARPS; ++k) {
-              al += s_part[grp][k][0];
-              be += s_part[grp][k][1];
-              gr += s_part[grp][k][2];
-              gi += s_part[grp][k][3];
-            }
-            const R g2 = gr * gr + gi * gi;
-            const R tol = (R)Ma * eps;
-            const R fl2 = (R)(floor_eps * floor_eps * s_fro[w]);
-            // rotate unless |gamma| <= tol sqrt(alpha beta), or a column is at the noise floor
-            // (|a|^2 <= floor_eps^2 ||A||_F^2: such columns cannot become orthogonal relative to
-            // their own norm and carry no information at this precision)
-            if (g2 > tol * tol * al * be && g2 > R(0) && fmin(al, be) > fl2) {
-              const R g = sqrt(g2), h = be - al;
-              // tan(theta) = 2 g sign(h) / (|h| + sqrt(h^2 + 4 g^2)): the smaller root
-              const R t = (h >= R(0) ? R(2) : R(-2)) * g / (fabs(h) + sqrt(h * h + R(4) * g2));
-              c = R(1) / sqrt(R(1) + t * t);
-              sv = c * t;
-              const R sg = sv / g;                 // s / |gamma|
-              ser = sg * gr;                        // s e^{-i phi}: e = conj(gamma) / |gamma|
-              sei = -sg * gi;
-              cer = c * gr / g;
-              cei = -c * gi / g;
-              flag = 1;
-            }
-          }
-          s_rot[grp][0] = flag;
-          s_rot[grp][1] = c;
-          s_rot[grp][2] = sv;
-          s_rot[grp][3] = ser;
-          s_rot[grp][4] = sei;
-          s_rot[grp][5] = cer;
-          s_rot[grp][6] = cei;
-        }
-        named_sync(1 + grp, 32 * GROUP_WARPS);
-        if (!real_pair || s_rot[grp][0] == R(0)) {
-          named_sync(1 + grp, 32 * GROUP_WARPS);
-          continue;
-        }
-        const R c = s_rot[grp][1], s = s_rot[grp][2], ser = s_rot[grp][3], sei = s_rot[grp][4];
-        const R cer = s_rot[grp][5], cei = s_rot[grp][6];
-        for (int r = gw * 32 + lane; r < Ma; r += 32 * GROUP_WARPS) {
-          const C2 x = __ldcg(ai + r), y = __ldcg(aj + r);
-          C2 nx, ny;
-          nx.x = c * x.x - (ser * y.x - sei * y.y);
-          nx.y = c * x.y - (ser * y.y + sei * y.x);
-          ny.x = s * x.x + (cer * y.x - cei * y.y);
-          ny.y = s * x.y + (cer * y.y + cei * y.x);
-          __stcg(ai + r, nx);
-          __stcg(aj + r, ny);
-        }
-        C2* vi = s_V[w] + (size_t)i * Na;
-        C2* vj = s_V[w] + (size_t)j * Na;
-        for (int r = gw * 32 + lane; r < Na; r += 32 * GROUP_WARPS) {
-          const C2 x = __ldcg(vi + r), y = __ldcg(vj + r);
-          C2 nx, ny;
-          nx.x = c * x.x - (ser * y.x - sei * y.y);
-          nx.y = c * x.y - (ser * y.y + sei * y.x);
-          ny.x = s * x.x + (cer * y.x - cei * y.y);
-          ny.y = s * x.y + (cer * y.y + cei * y.x);
-          __stcg(vi + r, nx);
-          __stcg(vj + r, ny);
-        }
-        if (gw == 0 && lane == 0) atomicAdd(&cnt[2 * w + par], 1);
       }
       if (!grid_barrier(gs, status)) return;
     }
