@@ -147,6 +147,25 @@ def step_flops(chis, kaps, N):
     return svd, other
 
 
+# ------------------------------------------------------------------------ replicas across ranks
+def aggregate(total_ms, site_steps_local, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: the timed region is the maximum over ranks,
+    the work is every rank's site-steps. Returns (value, max_ms)."""
+    import torch
+    world = 1
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([float(total_ms), float(site_steps_local)], dtype=torch.float64, device=device)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_ms, work = float(mx[0]), float(sm[1])
+    else:
+        work = float(site_steps_local)
+    return work / (total_ms / 1e3), total_ms
+
+
 # ------------------------------------------------------------------------ our arm
 LAUNCHES_PER_LAYER = {"fp64": 6, "fast": 18}
 
@@ -207,16 +226,12 @@ def run_ours(args, rank, world, local):
         step_ms, dims = _timed_window(eng, K, stream, flush, torch, n_chains)
     if world > 1:
         dist.barrier()
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value, total_ms = aggregate(float(np.sum(step_ms)), site_steps_per_step * K,
+                                dist if world > 1 else None, device="cuda")
     eng.sync()
     sweeps = eng.get_svd_sweeps()
     hist_fast, _ = eng.read_history(W, K + 1)
     eng.destroy()
-    value = site_steps_per_step * K * world / (total_ms / 1e3)
     fl_svd = fl_other = 0.0
     for per_chain in dims:
         for c, (chi, kap) in enumerate(per_chain):

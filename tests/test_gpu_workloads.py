@@ -1,0 +1,111 @@
+"""GPU checks of the other workloads: the 21-site XY chain (a bath on every site), the ensemble
+of independent chains, and the random augmented-MPS stress case.
+
+Element-by-element parity with the oracle runs at sizes the oracle finishes in seconds; the
+full-size runs check properties that hold at any size (trace, conservation of sum_n <s^z_n> for the
+isotropic XY chain with s^z baths, real expectation values, bond caps).
+"""
+import numpy as np
+import pytest
+
+from workloads import workload
+from workloads.configs import ChainSpec, Workload, BathSpec
+from oracle import model, problem as oprob
+from tests.gpu_helpers import OPS, oracle_envelope, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2201_05529_gb300 as pkg
+    pkg.build()
+    capi = pkg.load()
+    capi.use_torch_allocator()
+    return capi
+
+
+def _xy_chain(N, bath):
+    init = "".join("u" if n == N // 2 else "d" for n in range(N))
+    return ChainSpec(N=N, eps=(0.0,) * N, J=((1.0, 1.0, 0.0),) * (N - 1), init=init, baths=(bath,) * N)
+
+
+def test_xy_chain_with_a_bath_on_every_site_parity():
+    # the 21-site workload's bath (alpha=0.05, wc=3, T=0.8), kappa <= 16, chi <= 128, eps = 1e-6,
+    # dt = 0.1, on 9 sites for 5 steps (every bond runs the QR and LQ reductions)
+    w0 = workload("xy21_allbaths")
+    w = Workload("xy9", (_xy_chain(9, w0.chains[0].baths[0]),), dt=w0.dt, K=5, chi_max=w0.chi_max,
+                 eps=w0.eps, kappa_max=w0.kappa_max)
+    cis = oprob.build_inputs(w)
+    eng, obs, tr = run_gpu(w, cis, OPS)
+    ref = run_oracle(w, cis, OPS)[0]
+    err = np.abs(obs[:, 0, :9, :] - ref.obs).max(axis=(1, 2))
+    env = oracle_envelope(w, cis[0], OPS)
+    bad = np.nonzero(err > TOL + 10 * env)[0]
+    assert len(bad) == 0, (err, env)
+    eng.destroy()
+
+
+def test_xy21_full_size_properties():
+    # the 21-site workload itself (PT-MPO built by the library's host builder), first 12 steps:
+    # sum_n <s^z_n> / Tr rho is conserved, expectation values are real, and Tr rho stays within the
+    # PT-MPO compression error of 1 (kappa <= 16 on 21 baths: a few 1e-5 per bath and step)
+    import paper_2201_05529_gb300._capi as capi
+    from paper_2201_05529_gb300 import problem as pp
+    w = workload("xy21_allbaths", K=12)
+    chains, mpos = pp.build_problem(w)
+    eng = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, max_steps=w.K)
+    eng.set_observables([model.SZ])
+    eng.step(w.K)
+    obs, tr = eng.read_history(0, w.K + 1)
+    sz = (obs[:, 0, :, 0] / tr[:, 0, None]).real
+    tot = sz.sum(axis=1)
+    assert abs(tot[0] - (-19.0)) < 1e-12
+    assert np.max(np.abs(tot - tot[0])) < 1e-6
+    assert np.max(np.abs(obs.imag)) < 1e-8
+    assert np.max(np.abs(tr[:, 0] - 1)) < 21 * 2e-4
+    chi, kap = eng.get_dims(0)
+    assert chi.max() <= w.chi_max and kap.max() <= w.kappa_max
+    print("xy21: chi after 12 steps", list(chi))
+    eng.destroy()
+
+
+def test_ensemble_of_four_chains_twenty_steps():
+    w = workload("xyz_ensemble64", K=20)
+    w.chains = w.chains[:4]
+    cis = oprob.build_inputs(w)
+    eng, obs, tr = run_gpu(w, cis, OPS)
+    refs = run_oracle(w, cis, OPS)
+    for c, r in enumerate(refs):
+        N = cis[c].N
+        err = np.abs(obs[:, c, :N, :] - r.obs).max(axis=(1, 2))
+        env = oracle_envelope(w, cis[c], OPS)
+        bad = np.nonzero(err > TOL + 10 * env)[0]
+        assert len(bad) == 0, (c, err.max())
+    eng.destroy()
+
+
+def test_random_stress_state_singular_values():
+    # the stress workload's structure (Gaussian augmented MPS, Gaussian PT tensors, Haar gates) at
+    # N=8, chi=32, kappa=8 for 2 steps: bond dims and singular values against the oracle
+    w = workload("random32_stress", K=2)
+    w.random_state = dict(N=8, chi=32, kappa=8, K=2)
+    w.chi_max = 32
+    w.kappa_max = 8
+    cis = oprob.build_inputs(w)
+    eng, obs, tr = run_gpu(w, cis, OPS, K=2)
+    ref = run_oracle(w, cis, OPS, K=2)[0]
+    chi, _ = eng.get_dims(0)
+    assert list(chi) == list(ref.chis[-1])
+    worst = 0.0
+    for b in range(1, 8):
+        lam = eng.get_lambda(0, b)
+        worst = max(worst, float(np.max(np.abs(lam - ref.final_mps.lam[b]))))
+    print(f"random stress N=8: max |lambda - oracle| = {worst:.2e}")
+    assert worst < 1e-9
+    eng.destroy()
