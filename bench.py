@@ -260,7 +260,7 @@ def run_ours(args, rank, world, local):
     eng.sync()
     eng.set_timing(True)
     stage = np.zeros(9)
-    nk = min(K, 5)
+    nk = K
     for i in range(nk):
         flush.fill_(float(i))
         eng.step(1)
@@ -285,7 +285,7 @@ def run_ours(args, rank, world, local):
                 "svd_sweeps_last_step": {"fp64": [int(x) for x in sweeps[:, 0]],
                                          "fp32": [int(x) for x in sweeps[:, 1]]},
                 "stage_ms_per_step": {"site": stage[0], "blocks_qr": stage[1], "theta": stage[2],
-                                      "svd_fp64": stage[3], "svd_fp32": stage[7], "svd_reorth": stage[8],
+                                      "svd_fp64": stage[3], "svd_fp32": stage[7], "svd_precond": stage[8],
                                       "truncate": stage[4], "recover": stage[5], "readout": stage[6]}}
 
     # --- end to end through the C ABI: host inputs -> init (H2D) -> W+K steps -> history (D2H)

@@ -143,7 +143,8 @@ const char* pt_tebd_last_error(pt_tebd_t h);   /* h may be NULL: last global err
 /* Per-stage device time of the last pt_tebd_step call with timing enabled, in milliseconds:
  * [0] site contraction, [1] block build + QR, [2] theta + gate, [3] SVD (FP64 sweeps),
  * [4] truncation, [5] Gamma recovery, [6] readout, [7] SVD FP32 sweeps (fast path),
- * [8] SVD re-orthonormalisation (fast path). Timing mode launches eagerly (no graph). */
+ * [8] SVD preconditioning: pivoted QR and the U = D V / sigma finish, or the mixed path's FP64
+ * re-orthonormalisation. Timing mode launches eagerly (no graph). */
 int pt_tebd_set_timing(pt_tebd_t h, int enable);
 int pt_tebd_get_timing(pt_tebd_t h, double* ms9);
 

@@ -92,7 +92,8 @@ struct BondWork {
   float2* A32;             // fast path: FP32 copy of D for the bulk Jacobi sweeps
   float2* V32;             // fast path: FP32 right factor of those sweeps
   double2* G64;            // fast path: [k_cap^2] Gram / product scratch of the V re-orthonormalisation
-  double2* Y64;            // fast path: [max(mD,nD)_cap * k_cap] product scratch
+  double2* Y64;            // [max(mD,nD)_cap * k_cap] QR workspace / product scratch
+  int* qperm;              // [k_cap] column permutation of the pivoted QR
   int* info;               // [8] per-item: 0 mD, 1 nD, 2 transposed, 3 sweeps, 4-5 rotation counters
   int mL_cap, nL_cap, mR_cap, nR_cap, mD_cap, nD_cap, k_cap, pad2;
 };

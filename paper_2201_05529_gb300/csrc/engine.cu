@@ -82,6 +82,9 @@ struct pt_tebd {
   int rt_odd = 1, rt_even = 1, kc_odd = 1, kc_even = 1;   // fast path: theta tile / K-chunk caps
   std::vector<int*> bond_info;        // per bond (odd list, then even list): its info words
   bool mixed_svd = true;              // fast path: FP32 bulk sweeps + FP64 polish (PT_TEBD_SVD=fp64 disables)
+  bool precond = true;                // QR-preconditioned Jacobi (PT_TEBD_PRECOND=0 disables)
+  int qr_cluster = 1;
+  int qr_smem_cluster = 0;            // >0: the pivoted QR runs in cluster shared memory
   int kcap_odd = 1, kcap_even = 1, mcap_odd = 1, mcap_even = 1;
   unsigned* d_sync3 = nullptr;        // grid barrier state
   int* d_cnt_odd = nullptr;           // per-item rotation counters
@@ -228,6 +231,19 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n) {
     ev_begin(h, 3, &e);
     ptk::launch_mixed_fp64(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status,
                            std::max(1.1102230246251565e-16, std::min(5.9604644775390625e-8, 0.01 * h->opt.eps)), s);
+    ev_end(h, e);
+  } else if (h->grid_blocks > 0 && h->precond) {
+    // QR-preconditioned FP64 Jacobi: pivoted QR, Jacobi on R^H, then V_D = P U', U_D = D V_D / sigma
+    const int kc = work == h->d_odd ? h->kcap_odd : h->kcap_even, mc = work == h->d_odd ? h->mcap_odd : h->mcap_even;
+    ev_begin(h, 8, &e);
+    ptk::launch_qrcp_precondition(work, n, h->qr_cluster, h->qr_smem_cluster, kc, mc, h->T.status, s);
+    ev_end(h, e);
+    ev_begin(h, 3, &e);
+    ptk::launch_jacobi_grid(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status, s, 0, 1, 1,
+                            1.1102230246251565e-16, 3, /*on_b=*/1);
+    ev_end(h, e);
+    ev_begin(h, 8, &e);
+    ptk::launch_qrcp_finish(work, n, kc, mc, s);
     ev_end(h, e);
   } else {
     ev_begin(h, 3, &e);
@@ -624,10 +640,14 @@ int build(pt_tebd* h) {
         W.TB = h->dalloc(ptk::tc_pack_bytes(W.nD_cap, kcap, (int)h->opt.precision));
         W.A32 = (float2*)h->dalloc(sizeof(float2) * as);
         W.V32 = (float2*)h->dalloc(sizeof(float2) * vs);
+        if (!W.TA || !W.TB || !W.A32 || !W.V32) return h->fail(PT_ERR_OOM, "fast-path scratch");
+      }
+      {
+        const size_t ma = (size_t)std::max(W.mD_cap, W.nD_cap);
         W.G64 = (double2*)h->dalloc(sizeof(double2) * vs);
         W.Y64 = (double2*)h->dalloc(sizeof(double2) * ma * W.k_cap);
-        if (!W.TA || !W.TB || !W.A32 || !W.V32 || !W.G64 || !W.Y64)
-          return h->fail(PT_ERR_OOM, "fast-path scratch");
+        W.qperm = (int*)h->dalloc(sizeof(int) * W.k_cap);
+        if (!W.G64 || !W.Y64 || !W.qperm) return h->fail(PT_ERR_OOM, "SVD scratch");
       }
       if (W.nL_cap > 2048 || W.mR_cap > 2048)
         return h->fail(PT_ERR_CAPACITY, "QR reduction supports at most 2048 columns (4 chi <= 2048)");
@@ -658,6 +678,10 @@ int build(pt_tebd* h) {
     };
     caps(odd, &h->rt_odd, &h->kc_odd);
     caps(even, &h->rt_even, &h->kc_even);
+    const char* sv = getenv("PT_TEBD_SVD");
+    h->mixed_svd = sv && std::string(sv) == "mixed";
+  }
+  {
     auto dims = [&](const std::vector<BondWork>& v, int* kc, int* mc) {
       for (auto& W : v) {
         *kc = std::max(*kc, W.k_cap);
@@ -666,8 +690,13 @@ int build(pt_tebd* h) {
     };
     dims(odd, &h->kcap_odd, &h->mcap_odd);
     dims(even, &h->kcap_even, &h->mcap_even);
-    const char* sv = getenv("PT_TEBD_SVD");
-    h->mixed_svd = !(sv && std::string(sv) == "fp64");
+    const char* pc = getenv("PT_TEBD_PRECOND");
+    h->precond = !(pc && std::string(pc) == "0");
+    int k = std::max(h->kcap_odd, h->kcap_even);
+    h->qr_cluster = ptk::qrcp_cluster_size(std::max(1, std::min(16, (k + 31) / 32)));
+    const char* qv = getenv("PT_TEBD_QR");
+    if (!(qv && std::string(qv) == "global"))
+      h->qr_smem_cluster = ptk::qrcp_smem_cluster(std::max(h->mcap_odd, h->mcap_even), k);
   }
   // bond SVDs: whole-GPU cooperative kernel by default; PT_TEBD_JACOBI=cluster selects one
   // thread-block cluster per matrix instead

@@ -2,12 +2,17 @@
 //
 // The SVD is bound by FP64 arithmetic (1.2 TFLOP/s on GB300, ~7.9 GFLOP/s per SM), so every SM
 // must work on it even when a layer has only two bonds. One cooperative launch (one 1024-thread
-// CTA per SM) processes every matrix of the layer: in each round of the round-robin tournament the
-// column pairs of all matrices form one task list, each task handled by a group of 4 warps (one per
-// SM sub-partition) that split the rows; a grid barrier separates the rounds. Partial sums are
-// combined in a fixed order, so results are bitwise reproducible. Every barrier wait has a time
-// limit: on expiry the kernel records ST_TIMEOUT, raises an abort flag that releases every other
-// CTA, and returns.
+// CTA per SM) processes every matrix of the layer. The columns are grouped in blocks of two and a
+// round-robin tournament runs over the blocks: in each round the block pairs of all matrices form
+// one task list, each task handled by a slot of 8 warps (two groups of 4, one warp per SM
+// sub-partition in each, the rows split across them) that runs the task's four cross pairs (and,
+// in the first round of a sweep, the pair inside each block) in sub-rounds; a grid barrier
+// separates the rounds. Partial sums are combined in a fixed order, so results are bitwise
+// reproducible. Every barrier wait has a time limit: on expiry the kernel records ST_TIMEOUT,
+// raises an abort flag that releases every other CTA, and returns.
+//
+// on_b: the matrix is the square R^H left by the pivoted QR (qrcp.cu); only its left vectors are
+// wanted there, so the right factor is not accumulated.
 #include "kernels.h"
 
 namespace ptk {
@@ -99,7 +104,8 @@ __device__ __forceinline__ void item_shape(const BondWork& W, int* Ma, int* Na) 
 template <typename R>
 __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R>::T* V, int Ma, int Na, int i,
                                              int j, double fro, double floor_eps, int grp, int gw, int lane,
-                                             R (*s_part)[GROUP_WARPS][4], R (*s_rot)[8], int* cnt_slot) {
+                                             R (*s_part)[GROUP_WARPS][4], R (*s_rot)[8], int* cnt_slot,
+                                             bool with_v) {
   using C2 = typename Cx<R>::T;
   const R eps = Cx<R>::EPS;
   if (i > j) { const int tt = i; i = j; j = tt; }
@@ -188,7 +194,7 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
     __stcg(ai + r, nx);
     __stcg(aj + r, ny);
   }
-  for (int r = r0; r < Na; r += 32 * GROUP_WARPS) {
+  for (int r = r0; with_v && r < Na; r += 32 * GROUP_WARPS) {
     const C2 x = __ldcg(vi + r), y = __ldcg(vj + r);
     C2 nx, ny;
     nx.x = c * x.x - (ser * y.x - sei * y.y);
@@ -209,7 +215,7 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
 template <typename R>
 __global__ void __launch_bounds__(GRID_THREADS)
     k_jacobi_grid(const BondWork* work, int n_work, int max_sweeps, GridSync gs, int* cnt, int* status,
-                  int init_v, int finalize, double floor_eps, int sweep_slot) {
+                  int init_v, int finalize, double floor_eps, int sweep_slot, int on_b) {
   using C2 = typename Cx<R>::T;
   __shared__ int s_Na[MAX_ITEMS];
   __shared__ int s_Ma[MAX_ITEMS];
@@ -234,9 +240,9 @@ __global__ void __launch_bounds__(GRID_THREADS)
     int Ma, Na;
     item_shape(work[w], &Ma, &Na);
     s_Na[w] = Na;
-    s_Ma[w] = Ma;
+    s_Ma[w] = on_b ? Na : Ma;                 // on_b: the square R^H of the pivoted QR (G64)
     s_active[w] = Na >= 2;
-    s_A[w] = Cx<R>::A(work[w]);
+    s_A[w] = on_b ? (C2*)work[w].G64 : Cx<R>::A(work[w]);
     s_V[w] = Cx<R>::V(work[w]);
   }
   __syncthreads();
@@ -245,7 +251,7 @@ __global__ void __launch_bounds__(GRID_THREADS)
     const int gt = blockIdx.x * blockDim.x + tid, ngt = gridDim.x * blockDim.x;
     for (int w = 0; w < n_work; ++w) {
       const int Na = s_Na[w];
-      if (init_v) {
+      if (init_v && !on_b) {
         C2* V = s_V[w];
         for (size_t idx = gt; idx < (size_t)Na * Na; idx += ngt) {
           C2 v;
@@ -336,7 +342,7 @@ __global__ void __launch_bounds__(GRID_THREADS)
           else if (sr == 1) { i = i0 + sub; j = j0 + 1 - sub; }
           else { i = sub == 0 ? i0 : j0; j = i + 1; }          // pairs inside each block
           process_pair<R>(s_A[w], s_V[w], Ma, Na, i, j, s_fro[w], floor_eps, grp, gw, lane, s_part, s_rot,
-                          &cnt[2 * w + par]);
+                          &cnt[2 * w + par], !on_b);
           named_sync(9 + slot, 32 * GROUP_WARPS * 2);
         }
       }
@@ -422,7 +428,7 @@ int jacobi_grid_blocks() {
 
 void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3,
                         int* cnt, int* status, cudaStream_t st, int fp32, int init_v, int finalize,
-                        double floor_eps, int sweep_slot) {
+                        double floor_eps, int sweep_slot, int on_b) {
   // barrier arrival count and abort flag start at zero for every launch (the generation never resets)
   cudaMemsetAsync(sync3, 0, sizeof(unsigned), st);
   cudaMemsetAsync(sync3 + 2, 0, sizeof(unsigned), st);
@@ -438,10 +444,10 @@ void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sw
   cfg.numAttrs = 1;
   if (fp32)
     cudaLaunchKernelEx(&cfg, k_jacobi_grid<float>, work, n_work, max_sweeps, gs, cnt, status, init_v, finalize,
-                       floor_eps, sweep_slot);
+                       floor_eps, sweep_slot, 0);
   else
     cudaLaunchKernelEx(&cfg, k_jacobi_grid<double>, work, n_work, max_sweeps, gs, cnt, status, init_v, finalize,
-                       floor_eps, sweep_slot);
+                       floor_eps, sweep_slot, on_b);
 }
 
 }  // namespace ptk

@@ -39,7 +39,16 @@ int jacobi_grid_blocks();
 // floor_eps: unit roundoff of the noise floor; sweep_slot: info[] index for the sweep count
 void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3,
                         int* cnt, int* status, cudaStream_t st, int fp32 = 0, int init_v = 1, int finalize = 1,
-                        double floor_eps = 1.1102230246251565e-16, int sweep_slot = 3);
+                        double floor_eps = 1.1102230246251565e-16, int sweep_slot = 3, int on_b = 0);
+
+// QR preconditioning of the bond SVD (qrcp.cu): pivoted QR of D into Y64, B = R^H into G64;
+// after the Jacobi on B: V_D = P U', U_D = D V_D / sigma
+int qrcp_cluster_size(int want);
+int qrcp_smem_cluster(int m_cap, int n_cap);
+void launch_qrcp_precondition(const BondWork* work, int n_work, int cluster, int smem_cluster, int k_cap, int m_cap,
+                              int* status, cudaStream_t st);
+void launch_qrcp_finish(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st);
+void launch_mix_gemm_av(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st);
 
 // fast path: FP32 bulk sweeps + FP64 Newton-Schulz re-orthonormalisation + FP64 polish (mixed_svd.cu)
 void launch_mixed_fp32(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,

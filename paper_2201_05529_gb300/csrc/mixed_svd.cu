@@ -138,6 +138,12 @@ __global__ void k_mix_update(const BondWork* work, int n_work, int op) {
   }
 }
 
+// Y64 = A V (A: Ma x Na, V: Na x Na)
+void launch_mix_gemm_av(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st) {
+  const int tk = (k_cap + TB - 1) / TB, tmm = (m_cap + TB - 1) / TB;
+  k_mix_gemm<<<dim3(tmm, tk, n_work), 256, 0, st>>>(work, n_work, 2);
+}
+
 // stage 1: FP32 copy of D and the FP32 bulk sweeps (V32 from identity)
 void launch_mixed_fp32(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,
                        int* status, cudaStream_t st) {
