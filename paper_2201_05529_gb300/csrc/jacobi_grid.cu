@@ -99,75 +99,82 @@ __device__ __forceinline__ void item_shape(const BondWork& W, int* Ma, int* Na) 
 
 }  // namespace
 
-// One column pair (i, j) of matrix w, processed by the 4 warps of group grp (rows split across
-// them). Returns nothing; counts a rotation in cnt. Every warp of the group must call it.
+// Sum over the 32 lanes of two values at once (a reduce-scatter butterfly): lane 0 ends with the
+// total of a, lane 16 with the total of b; 5 shuffles and 5 adds instead of 10 and 10.
 template <typename R>
-__device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R>::T* V, int Ma, int Na, int i,
-                                             int j, double fro, double floor_eps, int grp, int gw, int lane,
-                                             R (*s_part)[GROUP_WARPS][4], R (*s_rot)[8], int* cnt_slot,
+__device__ __forceinline__ R wsum2(R a, R b, int lane) {
+  const bool hi = (lane & 16) != 0;
+  R keep = hi ? b : a;
+  keep += __shfl_xor_sync(0xffffffffu, hi ? a : b, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  return keep;
+}
+
+// One column pair (i, j) of matrix w, processed by the 4 warps of group grp (rows split across
+// them). nrm holds the squared column norms: they are read here, and rewritten (recomputed from
+// the rotated columns) when the pair rotates, so the dot phase only forms gamma = a_i^H a_j.
+// Counts a rotation in cnt. Every warp of the group must call it.
+template <typename R>
+__device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R>::T* V, double* nrm, int Ma,
+                                             int Na, int i, int j, double fro, double floor_eps, int grp, int gw,
+                                             int lane, R (*s_part)[GROUP_WARPS][4], R (*s_rot)[8], int* cnt_slot,
                                              bool with_v) {
   using C2 = typename Cx<R>::T;
   const R eps = Cx<R>::EPS;
   if (i > j) { const int tt = i; i = j; j = tt; }
   const bool real_pair = j < Na;        // uniform within the group
   if (!real_pair) return;
+  const bool leader = gw == 0 && lane == 0;
+  R al = 0, be = 0;
+  if (leader) {
+    al = (R)__ldcg(nrm + i);
+    be = (R)__ldcg(nrm + j);
+  }
   C2* ai = A + (size_t)i * Ma;
   C2* aj = A + (size_t)j * Ma;
   C2* vi = V + (size_t)i * Na;
   C2* vj = V + (size_t)j * Na;
   const int r0 = gw * 32 + lane;
   {
-    R al = 0, be = 0, gr = 0, gi = 0;
+    R gr = 0, gi = 0;
     for (int r = r0; r < Ma; r += 32 * GROUP_WARPS) {
       const C2 x = __ldcg(ai + r), y = __ldcg(aj + r);
-      al = fma(x.x, x.x, fma(x.y, x.y, al));
-      be = fma(y.x, y.x, fma(y.y, y.y, be));
       gr = fma(x.x, y.x, fma(x.y, y.y, gr));
       gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
     }
-    al = wsumd(al);
-    be = wsumd(be);
-    gr = wsumd(gr);
-    gi = wsumd(gi);
-    if (lane == 0) {
-      s_part[grp][gw][0] = al;
-      s_part[grp][gw][1] = be;
-      s_part[grp][gw][2] = gr;
-      s_part[grp][gw][3] = gi;
-    }
+    const R part = wsum2(gr, gi, lane);
+    if (lane == 0) s_part[grp][gw][0] = part;
+    if (lane == 16) s_part[grp][gw][1] = part;
   }
   named_sync(1 + grp, 32 * GROUP_WARPS);
   // one lane turns the partial sums (fixed order) into the rotation and shares it
-  if (gw == 0 && lane == 0) {
+  if (leader) {
     R flag = 0, c = 1, sv = 0, ser = 0, sei = 0, cer = 1, cei = 0;
-    if (real_pair) {
-      R al = 0, be = 0, gr = 0, gi = 0;
+    R gr = 0, gi = 0;
 #pragma unroll
-      for (int k = 0; k < GROUP_WARPS; ++k) {
-        al += s_part[grp][k][0];
-        be += s_part[grp][k][1];
-        gr += s_part[grp][k][2];
-        gi += s_part[grp][k][3];
-      }
-      const R g2 = gr * gr + gi * gi;
-      const R tol = (R)Ma * eps;
-      const R fl2 = (R)(floor_eps * floor_eps * fro);
-      // rotate unless |gamma| <= tol sqrt(alpha beta), or a column is at the noise floor
-      // (|a|^2 <= floor_eps^2 ||A||_F^2: such columns cannot become orthogonal relative to
-      // their own norm and carry no information at this precision)
-      if (g2 > tol * tol * al * be && g2 > R(0) && fmin(al, be) > fl2) {
-        const R g = sqrt(g2), h = be - al;
-        // tan(theta) = 2 g sign(h) / (|h| + sqrt(h^2 + 4 g^2)): the smaller root
-        const R t = (h >= R(0) ? R(2) : R(-2)) * g / (fabs(h) + sqrt(h * h + R(4) * g2));
-        c = R(1) / sqrt(R(1) + t * t);
-        sv = c * t;
-        const R sg = sv / g;                 // s / |gamma|
-        ser = sg * gr;                        // s e^{-i phi}: e = conj(gamma) / |gamma|
-        sei = -sg * gi;
-        cer = c * gr / g;
-        cei = -c * gi / g;
-        flag = 1;
-      }
+    for (int k = 0; k < GROUP_WARPS; ++k) {
+      gr += s_part[grp][k][0];
+      gi += s_part[grp][k][1];
+    }
+    const R g2 = gr * gr + gi * gi;
+    const R tol = (R)Ma * eps;
+    const R fl2 = (R)(floor_eps * floor_eps * fro);
+    // rotate unless |gamma| <= tol sqrt(alpha beta), or a column is at the noise floor
+    // (|a|^2 <= floor_eps^2 ||A||_F^2: such columns cannot become orthogonal relative to
+    // their own norm and carry no information at this precision)
+    if (g2 > tol * tol * al * be && g2 > R(0) && fmin(al, be) > fl2) {
+      const R g = sqrt(g2), h = be - al;
+      // tan(theta) = 2 g sign(h) / (|h| + sqrt(h^2 + 4 g^2)): the smaller root
+      const R t = (h >= R(0) ? R(2) : R(-2)) * g / (fabs(h) + sqrt(h * h + R(4) * g2));
+      c = R(1) / sqrt(R(1) + t * t);
+      sv = c * t;
+      const R sg = sv / g;                 // s / |gamma|
+      ser = sg * gr;                        // s e^{-i phi}: e = conj(gamma) / |gamma|
+      sei = -sg * gi;
+      cer = c * gr / g;
+      cei = -c * gi / g;
+      flag = 1;
     }
     s_rot[grp][0] = flag;
     s_rot[grp][1] = c;
@@ -178,12 +185,10 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
     s_rot[grp][6] = cei;
   }
   named_sync(1 + grp, 32 * GROUP_WARPS);
-  if (!real_pair || s_rot[grp][0] == R(0)) {
-    named_sync(1 + grp, 32 * GROUP_WARPS);
-    return;
-  }
+  if (s_rot[grp][0] == R(0)) return;
   const R c = s_rot[grp][1], s = s_rot[grp][2], ser = s_rot[grp][3], sei = s_rot[grp][4];
   const R cer = s_rot[grp][5], cei = s_rot[grp][6];
+  R na = 0, nb = 0;
   for (int r = r0; r < Ma; r += 32 * GROUP_WARPS) {
     const C2 x = __ldcg(ai + r), y = __ldcg(aj + r);
     C2 nx, ny;
@@ -193,6 +198,8 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
     ny.y = s * x.y + (cer * y.y + cei * y.x);
     __stcg(ai + r, nx);
     __stcg(aj + r, ny);
+    na = fma(nx.x, nx.x, fma(nx.y, nx.y, na));
+    nb = fma(ny.x, ny.x, fma(ny.y, ny.y, nb));
   }
   for (int r = r0; with_v && r < Na; r += 32 * GROUP_WARPS) {
     const C2 x = __ldcg(vi + r), y = __ldcg(vj + r);
@@ -204,7 +211,22 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
     __stcg(vi + r, nx);
     __stcg(vj + r, ny);
   }
-  if (gw == 0 && lane == 0) atomicAdd(cnt_slot, 1);
+  // the rotated columns' norms
+  const R part = wsum2(na, nb, lane);
+  if (lane == 0) s_part[grp][gw][2] = part;
+  if (lane == 16) s_part[grp][gw][3] = part;
+  named_sync(1 + grp, 32 * GROUP_WARPS);
+  if (leader) {
+    R sa = 0, sb = 0;
+#pragma unroll
+    for (int k = 0; k < GROUP_WARPS; ++k) {
+      sa += s_part[grp][k][2];
+      sb += s_part[grp][k][3];
+    }
+    __stcg(nrm + i, (double)sa);
+    __stcg(nrm + j, (double)sb);
+    atomicAdd(cnt_slot, 1);
+  }
 }
 
 // One-sided Jacobi over all matrices of a layer. R = double: FP64 on W.A / W.V (the FP64 path, and
@@ -341,8 +363,8 @@ __global__ void __launch_bounds__(GRID_THREADS)
           if (sr == 0) { i = i0 + sub; j = j0 + sub; }
           else if (sr == 1) { i = i0 + sub; j = j0 + 1 - sub; }
           else { i = sub == 0 ? i0 : j0; j = i + 1; }          // pairs inside each block
-          process_pair<R>(s_A[w], s_V[w], Ma, Na, i, j, s_fro[w], floor_eps, grp, gw, lane, s_part, s_rot,
-                          &cnt[2 * w + par], !on_b);
+          process_pair<R>(s_A[w], s_V[w], work[w].aux, Ma, Na, i, j, s_fro[w], floor_eps, grp, gw, lane, s_part,
+                          s_rot, &cnt[2 * w + par], !on_b);
           named_sync(9 + slot, 32 * GROUP_WARPS * 2);
         }
       }
