@@ -1,7 +1,7 @@
 // Whole-GPU one-sided Jacobi SVD for all bond matrices of one layer (App. A.2 (f-g)).
 //
 // The SVD is bound by FP64 arithmetic (1.2 TFLOP/s on GB300, ~7.9 GFLOP/s per SM), so every SM
-// must work on it even when a layer has only two bonds. One cooperative launch (one 1024-thread
+// must work on it even when a layer has only two bonds. One cooperative launch (one 512-thread
 // CTA per SM) processes every matrix of the layer. The columns are grouped in blocks of two and a
 // round-robin tournament runs over the blocks: in each round the block pairs of all matrices form
 // one task list, each task handled by a slot of 8 warps (two groups of 4, one warp per SM
@@ -19,9 +19,9 @@ namespace ptk {
 
 namespace {
 
-constexpr int GRID_THREADS = 1024;
+constexpr int GRID_THREADS = 512;
 constexpr int GROUP_WARPS = 4;
-constexpr int GROUPS = GRID_THREADS / 32 / GROUP_WARPS;    // 8 pair tasks per CTA at a time
+constexpr int GROUPS = GRID_THREADS / 32 / GROUP_WARPS;    // 4 pairs per CTA at a time (2 task slots)
 constexpr int MAX_ITEMS = 1024;
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;       // ~2 s at 2 GHz
 
@@ -32,21 +32,22 @@ struct GridSync {
 };
 
 // Grid-wide barrier for a cooperative launch; false when aborted (timeout here or elsewhere).
+// The arrival counter only grows (it is zeroed before each launch): barrier k of the launch is
+// complete once it reaches k * gridDim.x, so one atomic per CTA and polling of the same word
+// suffice. The abort flag and the time limit are checked every 64 polls.
 __device__ bool grid_barrier(const GridSync& gs, int* status) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    volatile unsigned* vgen = gs.gen;
-    const unsigned g = *vgen;
     __threadfence();
-    if (atomicAdd(gs.count, 1u) == gridDim.x - 1) {
-      *gs.count = 0;
-      __threadfence();
-      atomicAdd(gs.gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == g) {
+    const unsigned old = atomicAdd(gs.count, 1u);
+    const unsigned target = (old / gridDim.x + 1u) * gridDim.x;
+    volatile unsigned* vc = gs.count;
+    const long long t0 = clock64();
+    for (int it = 1;; ++it) {
+      if ((int)(*vc - target) >= 0) break;
+      if ((it & 63) == 0) {
         if (*(volatile int*)gs.abort) { ok = 0; break; }
         if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
           atomicOr(status, ST_TIMEOUT);
@@ -54,11 +55,9 @@ __device__ bool grid_barrier(const GridSync& gs, int* status) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
     __threadfence();
-    if (*(volatile int*)gs.abort) ok = 0;
     ok_s = ok;
   }
   __syncthreads();
@@ -136,9 +135,23 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
   C2* vi = V + (size_t)i * Na;
   C2* vj = V + (size_t)j * Na;
   const int r0 = gw * 32 + lane;
+  // the first RC rows of each lane stay in registers for the rotation (all of them when
+  // Ma <= RC * 128); the rest, if any, are read again
+  constexpr int RC = 2, STEP = 32 * GROUP_WARPS;
+  C2 xs[RC], ys[RC];
   {
     R gr = 0, gi = 0;
-    for (int r = r0; r < Ma; r += 32 * GROUP_WARPS) {
+#pragma unroll
+    for (int k = 0; k < RC; ++k) {
+      const int r = r0 + k * STEP;
+      if (r < Ma) {
+        xs[k] = __ldcg(ai + r);
+        ys[k] = __ldcg(aj + r);
+        gr = fma(xs[k].x, ys[k].x, fma(xs[k].y, ys[k].y, gr));
+        gi = fma(xs[k].x, ys[k].y, fma(-xs[k].y, ys[k].x, gi));
+      }
+    }
+    for (int r = r0 + RC * STEP; r < Ma; r += STEP) {
       const C2 x = __ldcg(ai + r), y = __ldcg(aj + r);
       gr = fma(x.x, y.x, fma(x.y, y.y, gr));
       gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
@@ -164,16 +177,16 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
     // (|a|^2 <= floor_eps^2 ||A||_F^2: such columns cannot become orthogonal relative to
     // their own norm and carry no information at this precision)
     if (g2 > tol * tol * al * be && g2 > R(0) && fmin(al, be) > fl2) {
-      const R g = sqrt(g2), h = be - al;
+      const R ig = rsqrt(g2), g = g2 * ig, h = be - al;    // ig = 1 / |gamma|
       // tan(theta) = 2 g sign(h) / (|h| + sqrt(h^2 + 4 g^2)): the smaller root
       const R t = (h >= R(0) ? R(2) : R(-2)) * g / (fabs(h) + sqrt(h * h + R(4) * g2));
-      c = R(1) / sqrt(R(1) + t * t);
+      c = rsqrt(R(1) + t * t);
       sv = c * t;
-      const R sg = sv / g;                 // s / |gamma|
+      const R sg = sv * ig, cg_ = c * ig;
       ser = sg * gr;                        // s e^{-i phi}: e = conj(gamma) / |gamma|
       sei = -sg * gi;
-      cer = c * gr / g;
-      cei = -c * gi / g;
+      cer = cg_ * gr;
+      cei = -cg_ * gi;
       flag = 1;
     }
     s_rot[grp][0] = flag;
@@ -189,8 +202,7 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
   const R c = s_rot[grp][1], s = s_rot[grp][2], ser = s_rot[grp][3], sei = s_rot[grp][4];
   const R cer = s_rot[grp][5], cei = s_rot[grp][6];
   R na = 0, nb = 0;
-  for (int r = r0; r < Ma; r += 32 * GROUP_WARPS) {
-    const C2 x = __ldcg(ai + r), y = __ldcg(aj + r);
+  auto rotate = [&](int r, C2 x, C2 y) {
     C2 nx, ny;
     nx.x = c * x.x - (ser * y.x - sei * y.y);
     nx.y = c * x.y - (ser * y.y + sei * y.x);
@@ -200,7 +212,13 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
     __stcg(aj + r, ny);
     na = fma(nx.x, nx.x, fma(nx.y, nx.y, na));
     nb = fma(ny.x, ny.x, fma(ny.y, ny.y, nb));
+  };
+#pragma unroll
+  for (int k = 0; k < RC; ++k) {
+    const int r = r0 + k * STEP;
+    if (r < Ma) rotate(r, xs[k], ys[k]);
   }
+  for (int r = r0 + RC * STEP; r < Ma; r += STEP) rotate(r, __ldcg(ai + r), __ldcg(aj + r));
   for (int r = r0; with_v && r < Na; r += 32 * GROUP_WARPS) {
     const C2 x = __ldcg(vi + r), y = __ldcg(vj + r);
     C2 nx, ny;
