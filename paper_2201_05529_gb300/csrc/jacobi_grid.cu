@@ -27,7 +27,6 @@ constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;       // ~2 s at 2 GHz
 
 struct GridSync {
   unsigned* count;
-  unsigned* gen;
   int* abort;
 };
 
@@ -111,8 +110,9 @@ __device__ __forceinline__ R wsum2(R a, R b, int lane) {
 }
 
 // One column pair (i, j) of matrix w, processed by the 4 warps of group grp (rows split across
-// them). nrm holds the squared column norms: they are read here, and rewritten (recomputed from
-// the rotated columns) when the pair rotates, so the dot phase only forms gamma = a_i^H a_j.
+// them). nrm holds the squared column norms: they are read here and, when the pair rotates,
+// updated by the rotation's closed form (or recomputed from the columns where that form cancels),
+// so the dot phase only forms gamma = a_i^H a_j.
 // Counts a rotation in cnt. Every warp of the group must call it.
 template <typename R>
 __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R>::T* V, double* nrm, int Ma,
@@ -187,7 +187,17 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
       sei = -sg * gi;
       cer = cg_ * gr;
       cei = -cg_ * gi;
-      flag = 1;
+      // the rotated columns' squared norms are al - t g and be + t g; where one of them drops
+      // below a quarter of its old value (cancellation), both are recomputed from the columns
+      const R tg = t * g, al2 = al - tg, be2 = be + tg;
+      if (al2 >= R(0.25) * al && be2 >= R(0.25) * be) {
+        flag = 1;
+        __stcg(nrm + i, (double)al2);
+        __stcg(nrm + j, (double)be2);
+        atomicAdd(cnt_slot, 1);
+      } else {
+        flag = 2;
+      }
     }
     s_rot[grp][0] = flag;
     s_rot[grp][1] = c;
@@ -201,6 +211,7 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
   if (s_rot[grp][0] == R(0)) return;
   const R c = s_rot[grp][1], s = s_rot[grp][2], ser = s_rot[grp][3], sei = s_rot[grp][4];
   const R cer = s_rot[grp][5], cei = s_rot[grp][6];
+  const bool renorm = s_rot[grp][0] == R(2);
   R na = 0, nb = 0;
   auto rotate = [&](int r, C2 x, C2 y) {
     C2 nx, ny;
@@ -210,8 +221,10 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
     ny.y = s * x.y + (cer * y.y + cei * y.x);
     __stcg(ai + r, nx);
     __stcg(aj + r, ny);
-    na = fma(nx.x, nx.x, fma(nx.y, nx.y, na));
-    nb = fma(ny.x, ny.x, fma(ny.y, ny.y, nb));
+    if (renorm) {
+      na = fma(nx.x, nx.x, fma(nx.y, nx.y, na));
+      nb = fma(ny.x, ny.x, fma(ny.y, ny.y, nb));
+    }
   };
 #pragma unroll
   for (int k = 0; k < RC; ++k) {
@@ -229,7 +242,8 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
     __stcg(vi + r, nx);
     __stcg(vj + r, ny);
   }
-  // the rotated columns' norms
+  if (!renorm) return;
+  // the rotated columns' norms, recomputed
   const R part = wsum2(na, nb, lane);
   if (lane == 0) s_part[grp][gw][2] = part;
   if (lane == 16) s_part[grp][gw][3] = part;
@@ -469,10 +483,10 @@ int jacobi_grid_blocks() {
 void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3,
                         int* cnt, int* status, cudaStream_t st, int fp32, int init_v, int finalize,
                         double floor_eps, int sweep_slot, int on_b) {
-  // barrier arrival count and abort flag start at zero for every launch (the generation never resets)
+  // the barrier's arrival counter and the abort flag start at zero for every launch
   cudaMemsetAsync(sync3, 0, sizeof(unsigned), st);
   cudaMemsetAsync(sync3 + 2, 0, sizeof(unsigned), st);
-  GridSync gs{sync3, sync3 + 1, (int*)(sync3 + 2)};
+  GridSync gs{sync3, (int*)(sync3 + 2)};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks, 1, 1);
   cfg.blockDim = dim3(GRID_THREADS, 1, 1);

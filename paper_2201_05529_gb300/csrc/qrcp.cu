@@ -35,6 +35,16 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
+// two lane sums at once: lane 0 ends with the total of a, lane 16 with that of b
+__device__ __forceinline__ double wsum2(double a, double b, int lane) {
+  const bool hi = (lane & 16) != 0;
+  double keep = hi ? b : a;
+  keep += __shfl_xor_sync(0xffffffffu, hi ? a : b, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  return keep;
+}
+
 }  // namespace
 
 // Column-pivoted Householder QR in place on X (Ma x Na col-major, Ma >= Na); X's upper triangle
@@ -182,6 +192,8 @@ __global__ void __launch_bounds__(1024) k_qrcp(const BondWork* work, int n_work)
   }
 }
 
+constexpr int QR_SMEM_THREADS = 512;
+
 // The same factorisation with the matrix held in the shared memory of a thread-block cluster.
 // Storage column s lives in CTA s % C at local index s / C. Pivoting is logical: the pivot column
 // is not moved; it is marked done and its position recorded (qp[j] = p), so R[i, j] is row i of
@@ -189,10 +201,13 @@ __global__ void __launch_bounds__(1024) k_qrcp(const BondWork* work, int n_work)
 // barrier: every CTA publishes its best remaining column (a double-buffered candidate), reads the
 // C candidates and the pivot column (distributed shared memory), and updates its own columns.
 // At the end every CTA writes the rows of B = R^H that belong to its columns.
-// Dynamic shared memory: X[lq_cap][m_cap] | hv[m_cap] | beta[lq_cap] (double2), nrm[lq_cap]
-// (double), qp[n_cap] | pos[n_cap] | done[lq_cap] (int).
-__global__ void __launch_bounds__(1024, 1) k_qrcp_smem(const BondWork* work, int n_work, int lq_cap, int m_cap,
-                                                       int n_cap, int* status) {
+// The partial column norms that pick the pivots are downdated, n <- n - |a_j|^2, and recomputed
+// where that cancels below sqrt(eps) of the last exact value (the safeguard of LAPACK's pivoted
+// QR); they only choose pivots. The reflector uses the exact norm of the pivot column.
+// Dynamic shared memory: X[lq_cap][m_cap] | hv[m_cap] | beta[lq_cap] (double2), nrm[lq_cap] |
+// nref[lq_cap] (double), qp[n_cap] | pos[n_cap] | done[lq_cap] (int).
+__global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
+    k_qrcp_smem(const BondWork* work, int n_work, int lq_cap, int m_cap, int n_cap, int* status) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int w = blockIdx.x / C;
@@ -210,12 +225,14 @@ __global__ void __launch_bounds__(1024, 1) k_qrcp_smem(const BondWork* work, int
   double2* hv = X + (size_t)lq_cap * m_cap;
   double2* betaL = hv + m_cap;
   double* nrm = (double*)(betaL + lq_cap);
-  int* qp = (int*)(nrm + lq_cap);
+  double* nref = nrm + lq_cap;
+  int* qp = (int*)(nref + lq_cap);
   int* pos = qp + n_cap;
   int* done = pos + n_cap;
   __shared__ double s_cval[2];
   __shared__ int s_cidx[2];
-  __shared__ double s_sc[8];                      // tau, ujinv.x, ujinv.y, pivot norm^2
+  __shared__ double s_sc[4];                      // tau, ujinv.x, ujinv.y
+  __shared__ double s_red[32];
   __shared__ int s_p;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int Ln = rank < Na ? (Na - rank + C - 1) / C : 0;
@@ -232,6 +249,7 @@ __global__ void __launch_bounds__(1024, 1) k_qrcp_smem(const BondWork* work, int
     sq = wsum(sq);
     if (lane == 0) {
       nrm[l] = sq;
+      nref[l] = sq;
       done[l] = 0;
     }
   }
@@ -273,18 +291,28 @@ __global__ void __launch_bounds__(1024, 1) k_qrcp_smem(const BondWork* work, int
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (lane == 0) {
-        s_p = bi;
-        s_sc[3] = best;
-      }
+      if (lane == 0) s_p = bi;
     }
     __syncthreads();
     const int p = s_p, owner = p % C, lp = p / C;
     const double2* src = cl.map_shared_rank(X, owner) + (size_t)lp * m_cap;
-    // 2. Householder scalars (identical inputs, identical arithmetic in every CTA)
+    // 2. the pivot column (rows j..) and its exact squared norm: every CTA sums the same values
+    //    in the same order, then derives the Householder scalars with identical arithmetic
+    {
+      double part = 0;
+      for (int r = j + tid; r < Ma; r += blockDim.x) {
+        const double2 xv = src[r];
+        hv[r] = xv;
+        part += xv.x * xv.x + xv.y * xv.y;
+      }
+      part = wsum(part);
+      if (lane == 0) s_red[wid] = part;
+    }
+    __syncthreads();
     if (tid == 0) {
-      const double nrm2 = s_sc[3];
-      const double2 alpha = src[j];
+      double nrm2 = 0;
+      for (int k = 0; k < nw; ++k) nrm2 += s_red[k];
+      const double2 alpha = hv[j];
       const double aabs = sqrt(alpha.x * alpha.x + alpha.y * alpha.y), xn = sqrt(nrm2);
       double tau = 0.0;
       double2 beta = alpha, ujinv = make_double2(0.0, 0.0);
@@ -309,43 +337,47 @@ __global__ void __launch_bounds__(1024, 1) k_qrcp_smem(const BondWork* work, int
     __syncthreads();
     const double tau = s_sc[0];
     const double2 ujinv = make_double2(s_sc[1], s_sc[2]);
-    // 3. the Householder vector u (u_j = 1) from the pivot column
-    if (tau != 0.0)
-      for (int r = j + tid; r < Ma; r += blockDim.x) {
-        double2 u = make_double2(1.0, 0.0);
-        if (r != j) {
-          const double2 xv = src[r];
-          u = make_double2(xv.x * ujinv.x - xv.y * ujinv.y, xv.x * ujinv.y + xv.y * ujinv.x);
-        }
-        hv[r] = u;
+    // 3. the Householder vector u = x / u_j (u_j = 1)
+    if (tau != 0.0) {
+      for (int r = j + 1 + tid; r < Ma; r += blockDim.x) {
+        const double2 xv = hv[r];
+        hv[r] = make_double2(xv.x * ujinv.x - xv.y * ujinv.y, xv.x * ujinv.y + xv.y * ujinv.x);
       }
+      if (tid == 0) hv[j] = make_double2(1.0, 0.0);
+    }
     __syncthreads();
-    // 4. own remaining columns: a <- a - tau u (u^H a); new partial norms over rows > j
-    if (tau != 0.0)
-      for (int l = wid; l < Ln; l += nw) {
-        if (done[l]) continue;
-        double2* a = X + (size_t)l * m_cap;
+    // 4. own remaining columns: a <- a - tau u (u^H a); partial norms over rows > j
+    for (int l = wid; l < Ln; l += nw) {
+      if (done[l]) continue;
+      double2* a = X + (size_t)l * m_cap;
+      if (tau != 0.0) {
         double sr = 0, si = 0;
         for (int r = j + lane; r < Ma; r += 32) {
           const double2 u = hv[r], av = a[r];
-          sr += u.x * av.x + u.y * av.y;
-          si += u.x * av.y - u.y * av.x;
+          sr = fma(u.x, av.x, fma(u.y, av.y, sr));
+          si = fma(u.x, av.y, fma(-u.y, av.x, si));
         }
-        sr = wsum(sr);
-        si = wsum(si);
-        const double tr_ = tau * sr, ti_ = tau * si;
-        double nn = 0;
+        const double part = wsum2(sr, si, lane);
+        const double tr_ = tau * __shfl_sync(0xffffffffu, part, 0), ti_ = tau * __shfl_sync(0xffffffffu, part, 16);
         for (int r = j + lane; r < Ma; r += 32) {
           const double2 u = hv[r];
           double2 av = a[r];
           av.x -= u.x * tr_ - u.y * ti_;
           av.y -= u.x * ti_ + u.y * tr_;
           a[r] = av;
-          if (r > j) nn += av.x * av.x + av.y * av.y;
         }
-        nn = wsum(nn);
-        if (lane == 0) nrm[l] = nn;
+        __syncwarp();
       }
+      const double2 ajv = a[j];
+      double nn = nrm[l] - (ajv.x * ajv.x + ajv.y * ajv.y);
+      if (nn <= 1.4901161193847656e-8 * nref[l]) {     // cancellation: recompute
+        double sq = 0;
+        for (int r = j + 1 + lane; r < Ma; r += 32) sq += a[r].x * a[r].x + a[r].y * a[r].y;
+        nn = wsum(sq);
+        if (lane == 0) nref[l] = nn;
+      }
+      if (lane == 0) nrm[l] = nn;
+    }
     __syncthreads();
     publish(par ^ 1);
     cl.sync();                                    // candidates published; pivot column reads done
@@ -432,7 +464,8 @@ static cudaLaunchConfig_t qr_cfg(int n_work, int cluster, cudaStream_t st, cudaL
 }
 
 static size_t qr_smem_bytes(int lq, int m_cap, int n_cap) {
-  return sizeof(double2) * ((size_t)lq * m_cap + m_cap + lq) + sizeof(double) * lq + sizeof(int) * (2 * (size_t)n_cap + lq);
+  return sizeof(double2) * ((size_t)lq * m_cap + m_cap + lq) + sizeof(double) * 2 * lq +
+         sizeof(int) * (2 * (size_t)n_cap + lq);
 }
 
 // Cluster size for the shared-memory factorisation of matrices up to m_cap x n_cap; 0 if they do
@@ -450,7 +483,7 @@ int qrcp_smem_cluster(int m_cap, int n_cap) {
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c, 1, 1);
-    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.blockDim = dim3(QR_SMEM_THREADS, 1, 1);
     cfg.dynamicSmemBytes = bytes;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = c;
@@ -484,6 +517,7 @@ void launch_qrcp_precondition(const BondWork* work, int n_work, int cluster, int
   if (smem_cluster > 0) {
     const int lq = (k_cap + smem_cluster - 1) / smem_cluster;
     cudaLaunchConfig_t cfg = qr_cfg(n_work, smem_cluster, st, at);
+    cfg.blockDim = dim3(QR_SMEM_THREADS, 1, 1);
     cfg.dynamicSmemBytes = qr_smem_bytes(lq, m_cap, k_cap);
     cudaLaunchKernelEx(&cfg, k_qrcp_smem, work, n_work, lq, m_cap, k_cap, status);
     return;
