@@ -177,19 +177,22 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
     // (|a|^2 <= floor_eps^2 ||A||_F^2: such columns cannot become orthogonal relative to
     // their own norm and carry no information at this precision)
     if (g2 > tol * tol * al * be && g2 > R(0) && fmin(al, be) > fl2) {
-      const R ig = rsqrt(g2), g = g2 * ig, h = be - al;    // ig = 1 / |gamma|
-      // tan(theta) = 2 g sign(h) / (|h| + sqrt(h^2 + 4 g^2)): the smaller root
-      const R t = (h >= R(0) ? R(2) : R(-2)) * g / (fabs(h) + sqrt(h * h + R(4) * g2));
-      c = rsqrt(R(1) + t * t);
-      sv = c * t;
-      const R sg = sv * ig, cg_ = c * ig;
+      // smaller root of the rotation equation: with q = sqrt(h^2 + 4 g^2) and w = q + |h|,
+      // |s| / g = sqrt(2 / (q w)), c = w |s| / (2 g) and t g = 2 g^2 sign(h) / w (two dependent
+      // long operations instead of four)
+      const R ig = rsqrt(g2), h = be - al, ah = fabs(h);          // ig = 1 / |gamma|
+      const R q = sqrt(h * h + R(4) * g2), wq = q + ah;
+      const R sgm = rsqrt(R(0.5) * q * wq);
+      const R sgn = h >= R(0) ? R(1) : R(-1);
+      const R sg = sgn * sgm;                                     // s / |gamma|
+      c = R(0.5) * wq * sgm;
+      sv = sg * g2 * ig;
       ser = sg * gr;                        // s e^{-i phi}: e = conj(gamma) / |gamma|
       sei = -sg * gi;
+      const R cg_ = c * ig;
       cer = cg_ * gr;
       cei = -cg_ * gi;
-      // the rotated columns' squared norms are al - t g and be + t g; where one of them drops
-      // below a quarter of its old value (cancellation), both are recomputed from the columns
-      const R tg = t * g, al2 = al - tg, be2 = be + tg;
+      const R tg = sgn * g2 * sgm * sgm * q, al2 = al - tg, be2 = be + tg;
       if (al2 >= R(0.25) * al && be2 >= R(0.25) * be) {
         flag = 1;
         __stcg(nrm + i, (double)al2);

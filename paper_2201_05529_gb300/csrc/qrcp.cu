@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
   int* done = pos + n_cap;
   __shared__ double s_cval[2];
   __shared__ int s_cidx[2];
-  __shared__ double s_sc[4];                      // tau, ujinv.x, ujinv.y
+  __shared__ double s_sc[1];                      // kappa of the step's reflector
   __shared__ double s_red[32];
   __shared__ int s_p;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -310,24 +310,28 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
     }
     __syncthreads();
     if (tid == 0) {
+      // H = I - kappa v v^H with v = x - beta e_j, beta = -phase(alpha) ||x||:
+      // v^H v = 2 ||x|| (||x|| + |alpha|), so kappa = 1 / (||x|| (||x|| + |alpha|))
       double nrm2 = 0;
       for (int k = 0; k < nw; ++k) nrm2 += s_red[k];
       const double2 alpha = hv[j];
-      const double aabs = sqrt(alpha.x * alpha.x + alpha.y * alpha.y), xn = sqrt(nrm2);
-      double tau = 0.0;
-      double2 beta = alpha, ujinv = make_double2(0.0, 0.0);
-      if (xn > 0.0) {
+      const double a2 = alpha.x * alpha.x + alpha.y * alpha.y;
+      double kap = 0.0;
+      double2 beta = alpha;
+      if (nrm2 > 0.0) {
+        const double xn = sqrt(nrm2);
         double2 ph = make_double2(1.0, 0.0);
-        if (aabs > 0.0) ph = make_double2(alpha.x / aabs, alpha.y / aabs);
+        double aabs = 0.0;
+        if (a2 > 0.0) {
+          const double ia = rsqrt(a2);
+          aabs = a2 * ia;
+          ph = make_double2(alpha.x * ia, alpha.y * ia);
+        }
         beta = make_double2(-ph.x * xn, -ph.y * xn);
-        const double2 uj = make_double2(ph.x * (aabs + xn), ph.y * (aabs + xn));   // alpha - beta
-        const double uj2 = uj.x * uj.x + uj.y * uj.y;
-        tau = 2.0 * uj2 / (nrm2 - aabs * aabs + uj2);
-        ujinv = make_double2(uj.x / uj2, -uj.y / uj2);
+        kap = 1.0 / (xn * (xn + aabs));
+        hv[j] = make_double2(ph.x * (aabs + xn), ph.y * (aabs + xn));     // v_j = alpha - beta
       }
-      s_sc[0] = tau;
-      s_sc[1] = ujinv.x;
-      s_sc[2] = ujinv.y;
+      s_sc[0] = kap;
       qp[j] = p;
       if (rank == owner) {
         betaL[lp] = beta;
@@ -335,22 +339,12 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
       }
     }
     __syncthreads();
-    const double tau = s_sc[0];
-    const double2 ujinv = make_double2(s_sc[1], s_sc[2]);
-    // 3. the Householder vector u = x / u_j (u_j = 1)
-    if (tau != 0.0) {
-      for (int r = j + 1 + tid; r < Ma; r += blockDim.x) {
-        const double2 xv = hv[r];
-        hv[r] = make_double2(xv.x * ujinv.x - xv.y * ujinv.y, xv.x * ujinv.y + xv.y * ujinv.x);
-      }
-      if (tid == 0) hv[j] = make_double2(1.0, 0.0);
-    }
-    __syncthreads();
-    // 4. own remaining columns: a <- a - tau u (u^H a); partial norms over rows > j
+    const double kap = s_sc[0];
+    // 3. own remaining columns: a <- a - kappa v (v^H a); partial norms over rows > j
     for (int l = wid; l < Ln; l += nw) {
       if (done[l]) continue;
       double2* a = X + (size_t)l * m_cap;
-      if (tau != 0.0) {
+      if (kap != 0.0) {
         double sr = 0, si = 0;
         for (int r = j + lane; r < Ma; r += 32) {
           const double2 u = hv[r], av = a[r];
@@ -358,7 +352,7 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
           si = fma(u.x, av.y, fma(-u.y, av.x, si));
         }
         const double part = wsum2(sr, si, lane);
-        const double tr_ = tau * __shfl_sync(0xffffffffu, part, 0), ti_ = tau * __shfl_sync(0xffffffffu, part, 16);
+        const double tr_ = kap * __shfl_sync(0xffffffffu, part, 0), ti_ = kap * __shfl_sync(0xffffffffu, part, 16);
         for (int r = j + lane; r < Ma; r += 32) {
           const double2 u = hv[r];
           double2 av = a[r];
