@@ -85,6 +85,7 @@ struct pt_tebd {
   bool precond = true;                // QR-preconditioned Jacobi (PT_TEBD_PRECOND=0 disables)
   int qr_cluster = 1;
   int qr_smem_cluster = 0;            // >0: the pivoted QR runs in cluster shared memory
+  bool qr_grid_odd = false, qr_grid_even = false;   // the pivoted QR runs on the whole GPU
   int kcap_odd = 1, kcap_even = 1, mcap_odd = 1, mcap_even = 1;
   unsigned* d_sync3 = nullptr;        // grid barrier state
   int* d_cnt_odd = nullptr;           // per-item rotation counters
@@ -236,7 +237,10 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n) {
     // QR-preconditioned FP64 Jacobi: pivoted QR, Jacobi on R^H, then V_D = P U', U_D = D V_D / sigma
     const int kc = work == h->d_odd ? h->kcap_odd : h->kcap_even, mc = work == h->d_odd ? h->mcap_odd : h->mcap_even;
     ev_begin(h, 8, &e);
-    ptk::launch_qrcp_precondition(work, n, h->qr_cluster, h->qr_smem_cluster, kc, mc, h->T.status, s);
+    if (work == h->d_odd ? h->qr_grid_odd : h->qr_grid_even)
+      ptk::launch_qrcp_grid(work, n, h->grid_blocks, h->d_sync3, h->T.status, s);
+    else
+      ptk::launch_qrcp_precondition(work, n, h->qr_cluster, h->qr_smem_cluster, kc, mc, h->T.status, s);
     ev_end(h, e);
     ev_begin(h, 3, &e);
     ptk::launch_jacobi_grid(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status, s, 0, 1, 1,
@@ -703,6 +707,20 @@ int build(pt_tebd* h) {
   const char* jv = getenv("PT_TEBD_JACOBI");
   const bool want_cluster = jv && std::string(jv) == "cluster";
   h->grid_blocks = (!want_cluster && std::max(h->n_odd, h->n_even) <= 1024) ? ptk::jacobi_grid_blocks() : 0;
+  {
+    // pivoted QR on the whole GPU where the layer's columns fit one per warp (PT_TEBD_QR=cluster or
+    // =global selects the cluster shared-memory or the global-memory kernel)
+    const char* qv = getenv("PT_TEBD_QR");
+    const bool qr_any = !(qv && (std::string(qv) == "cluster" || std::string(qv) == "global"));
+    const bool ok = qr_any && h->grid_blocks > 0 && ptk::qrcp_grid_ok();
+    auto fits = [&](const std::vector<BondWork>& v, int mc) {
+      int tot = 0;
+      for (auto& W : v) tot += W.k_cap;
+      return ok && !v.empty() && ptk::qrcp_grid_fits((int)v.size(), mc, tot, h->grid_blocks);
+    };
+    h->qr_grid_odd = fits(odd, h->mcap_odd);
+    h->qr_grid_even = fits(even, h->mcap_even);
+  }
   h->d_sync3 = (unsigned*)h->dalloc(sizeof(unsigned) * 4);
   h->d_cnt_odd = (int*)h->dalloc(sizeof(int) * 2 * std::max(1, h->n_odd));
   h->d_cnt_even = (int*)h->dalloc(sizeof(int) * 2 * std::max(1, h->n_even));

@@ -13,6 +13,7 @@
 //
 // on_b: the matrix is the square R^H left by the pivoted QR (qrcp.cu); only its left vectors are
 // wanted there, so the right factor is not accumulated.
+#include "grid_sync.cuh"
 #include "kernels.h"
 
 namespace ptk {
@@ -23,45 +24,6 @@ constexpr int GRID_THREADS = 512;
 constexpr int GROUP_WARPS = 4;
 constexpr int GROUPS = GRID_THREADS / 32 / GROUP_WARPS;    // 4 pairs per CTA at a time (2 task slots)
 constexpr int MAX_ITEMS = 1024;
-constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;       // ~2 s at 2 GHz
-
-struct GridSync {
-  unsigned* count;
-  int* abort;
-};
-
-// Grid-wide barrier for a cooperative launch; false when aborted (timeout here or elsewhere).
-// The arrival counter only grows (it is zeroed before each launch): barrier k of the launch is
-// complete once it reaches k * gridDim.x, so one atomic per CTA and polling of the same word
-// suffice. The abort flag and the time limit are checked every 64 polls.
-__device__ bool grid_barrier(const GridSync& gs, int* status) {
-  __shared__ int ok_s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    __threadfence();
-    const unsigned old = atomicAdd(gs.count, 1u);
-    const unsigned target = (old / gridDim.x + 1u) * gridDim.x;
-    volatile unsigned* vc = gs.count;
-    const long long t0 = clock64();
-    for (int it = 1;; ++it) {
-      if ((int)(*vc - target) >= 0) break;
-      if ((it & 63) == 0) {
-        if (*(volatile int*)gs.abort) { ok = 0; break; }
-        if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
-          atomicOr(status, ST_TIMEOUT);
-          atomicExch(gs.abort, 1);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    ok_s = ok;
-  }
-  __syncthreads();
-  return ok_s != 0;
-}
 
 template <typename R>
 __device__ __forceinline__ R wsumd(R v) {

@@ -33,7 +33,7 @@ void launch_jacobi_cluster(const BondWork* work, int n_work, int cluster, int ma
                            cudaStream_t st);
 
 // whole-GPU FP64 bond SVD (jacobi_grid.cu): blocks = one per SM (0 if not co-schedulable);
-// sync3: 3 words of device memory (arrival count, generation, abort flag); cnt: 2 ints per item
+// sync3: 3 words of device memory (arrival count, unused, abort flag); cnt: 2 ints per item
 int jacobi_grid_blocks();
 // fp32: sweeps in FP32 on A32/V32; init_v: start from V = I; finalize: sigma, U, order;
 // floor_eps: unit roundoff of the noise floor; sweep_slot: info[] index for the sweep count
@@ -45,6 +45,10 @@ void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sw
 // after the Jacobi on B: V_D = P U', U_D = D V_D / sigma
 int qrcp_cluster_size(int want);
 int qrcp_smem_cluster(int m_cap, int n_cap);
+// whole-GPU variant (cooperative, one CTA per SM): usable when qrcp_grid_ok() and the layer fits
+int qrcp_grid_ok();
+int qrcp_grid_fits(int n_work, int m_cap, int total_cols_cap, int blocks);
+void launch_qrcp_grid(const BondWork* work, int n_work, int blocks, unsigned* sync3, int* status, cudaStream_t st);
 void launch_qrcp_precondition(const BondWork* work, int n_work, int cluster, int smem_cluster, int k_cap, int m_cap,
                               int* status, cudaStream_t st);
 void launch_qrcp_finish(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st);

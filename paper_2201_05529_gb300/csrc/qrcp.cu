@@ -14,6 +14,7 @@
 //      the state error stays at rounding level; Q is never formed.
 #include <cooperative_groups.h>
 
+#include "grid_sync.cuh"
 #include "kernels.h"
 
 namespace cg = cooperative_groups;
@@ -394,6 +395,264 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
   cl.sync();                                      // no CTA leaves while its memory may be read
 }
 
+constexpr int QRG_THREADS = 512;
+constexpr int QRG_WARPS = QRG_THREADS / 32;
+constexpr int QRG_MAX_ITEMS = 256;
+constexpr int QRG_RC = 8;                 // rows per lane held in registers: Ma <= 256
+
+// The same factorisation for every matrix of a layer on the whole GPU (a cooperative launch, one
+// 512-thread CTA per SM): the concatenated columns of all matrices are split into equal ranges,
+// one range per CTA and one column per warp. A warp keeps its column's rows j.. in registers (a
+// one-row shift between steps) and writes them back to the workspace (Y64), where other CTAs
+// read pivot columns. Step j: every CTA picks the pivot of each matrix it holds columns of from
+// the partial norms (same values, same order everywhere), reads the pivot column and its exact
+// norm, and its warps apply the reflector; one grid barrier per step. The partial norms are
+// double-buffered (aux and sig alternate: step j reads one and writes the other, so a CTA still
+// choosing step j's pivot never sees step j+1's values); finished columns write -1. The pivot's owner records qperm[j] and beta_j (in V, free until the finish).
+// Finally every warp writes its column of B = R^H.
+__global__ void __launch_bounds__(QRG_THREADS, 1)
+    k_qrcp_grid(const BondWork* work, int n_work, GridSync gs, int* status) {
+  extern __shared__ double2 hv[];
+  __shared__ int s_off[QRG_MAX_ITEMS + 1];
+  __shared__ int s_Ma[QRG_MAX_ITEMS];
+  __shared__ int s_maxna;
+  __shared__ double s_red[QRG_WARPS];
+  __shared__ double s_kap;
+  __shared__ int s_p, s_own;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (n_work > QRG_MAX_ITEMS) {
+    if (blockIdx.x == 0 && tid == 0) atomicOr(status, ST_CAPACITY);
+    return;
+  }
+  if (tid == 0) {
+    int o = 0, mx = 0;
+    for (int w = 0; w < n_work; ++w) {
+      int Ma, Na;
+      shape(work[w], &Ma, &Na);
+      if (Ma > 32 * QRG_RC) {                // the host never launches such a layer here
+        if (blockIdx.x == 0) atomicOr(status, ST_CAPACITY);
+        Na = 0;
+      }
+      s_off[w] = o;
+      s_Ma[w] = Ma;
+      o += Na;
+      mx = max(mx, Na);
+    }
+    s_off[n_work] = o;
+    s_maxna = mx;
+  }
+  __syncthreads();
+  const int total = s_off[n_work];
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  if (per > QRG_WARPS) {
+    if (blockIdx.x == 0 && tid == 0) atomicOr(status, ST_CAPACITY);
+    return;                                   // uniform: every CTA sees the same total
+  }
+  const int g0 = min(total, (int)blockIdx.x * per), g1 = min(total, g0 + per);
+  // this warp's column (w_me, s_me), if any
+  const int gme = g0 + wid;
+  const bool have = wid < per && gme < g1;
+  int w_me = 0;
+  if (have) {
+    int lo = 0, hi = n_work - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= gme) lo = mid;
+      else hi = mid - 1;
+    }
+    w_me = lo;
+  }
+  const int s_me = gme - s_off[w_me];
+  const int Ma_me = have ? s_Ma[w_me] : 0;
+  double2 c[QRG_RC];
+  double nrm_me = 0, nref_me = 0;
+  bool done = !have;
+  if (have) {
+    const BondWork& W = work[w_me];
+    double sq = 0;
+#pragma unroll
+    for (int k = 0; k < QRG_RC; ++k) {
+      const int r = lane + 32 * k;
+      c[k] = make_double2(0.0, 0.0);
+      if (r < Ma_me) {
+        c[k] = W.A[r + (size_t)s_me * Ma_me];
+        __stcg(W.Y64 + r + (size_t)s_me * Ma_me, c[k]);
+        sq += c[k].x * c[k].x + c[k].y * c[k].y;
+      }
+    }
+    sq = wsum(sq);
+    nrm_me = nref_me = sq;
+    if (lane == 0) __stcg(W.aux + s_me, sq);       // step 0 reads aux
+  }
+  // the matrices this CTA holds columns of: w_lo..w_hi (none when g0 == g1)
+  auto item_of = [&](int g) {
+    int lo = 0, hi = n_work - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo;
+  };
+  const int w_lo = g0 < g1 ? item_of(g0) : 0;
+  const int w_hi = g0 < g1 ? item_of(g1 - 1) : -1;
+  if (!grid_barrier(gs, status)) return;
+  const int maxna = s_maxna;
+  for (int j = 0; j < maxna; ++j) {
+    for (int w = w_lo; w <= w_hi; ++w) {
+      const int Na = s_off[w + 1] - s_off[w], Ma = s_Ma[w];
+      if (j >= Na) continue;                  // uniform across the CTA
+      const BondWork& W = work[w];
+      const double2* X = W.Y64;
+      const double* nrm_cur = (j & 1) ? W.sig : W.aux;
+      double* nrm_nxt = (j & 1) ? W.aux : W.sig;
+      // (a) pivot: largest remaining partial norm, smallest index on ties (Na <= 256: all loads
+      //     of a lane are issued before the first comparison)
+      if (wid == 0) {
+        double best = -1.0;
+        int bi = 0x7fffffff;
+        double v[QRG_RC];
+#pragma unroll
+        for (int k = 0; k < QRG_RC; ++k) {
+          const int i = lane + 32 * k;
+          v[k] = i < Na ? __ldcg(nrm_cur + i) : -2.0;
+        }
+#pragma unroll
+        for (int k = 0; k < QRG_RC; ++k)
+          if (v[k] > best) { best = v[k]; bi = lane + 32 * k; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) s_p = bi;
+      }
+      __syncthreads();
+      const int p = s_p;
+      // (b) the pivot column (rows j..) and its exact norm, summed in the same order everywhere
+      {
+        double part = 0;
+        for (int r = j + tid; r < Ma; r += blockDim.x) {
+          const double2 xv = __ldcg(X + r + (size_t)p * Ma);
+          hv[r] = xv;
+          part += xv.x * xv.x + xv.y * xv.y;
+        }
+        part = wsum(part);
+        if (lane == 0) s_red[wid] = part;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double nrm2 = 0;
+        for (int k = 0; k < QRG_WARPS; ++k) nrm2 += s_red[k];
+        const double2 alpha = hv[j];
+        const double a2 = alpha.x * alpha.x + alpha.y * alpha.y;
+        double kap = 0.0;
+        double2 beta = alpha;
+        if (nrm2 > 0.0) {
+          const double xn = sqrt(nrm2);
+          double2 ph = make_double2(1.0, 0.0);
+          double aabs = 0.0;
+          if (a2 > 0.0) {
+            const double ia = rsqrt(a2);
+            aabs = a2 * ia;
+            ph = make_double2(alpha.x * ia, alpha.y * ia);
+          }
+          beta = make_double2(-ph.x * xn, -ph.y * xn);
+          kap = 1.0 / (xn * (xn + aabs));
+          hv[j] = make_double2(ph.x * (aabs + xn), ph.y * (aabs + xn));
+        }
+        s_kap = kap;
+        const int gp = s_off[w] + p;
+        s_own = -1;
+        if (gp >= g0 && gp < g1) {              // this CTA owns the pivot column
+          s_own = gp - g0;
+          __stcg(W.qperm + j, p);
+          __stcg(W.V + j, beta);
+        }
+      }
+      __syncthreads();
+      const double kap = s_kap;
+      if (have && w_me == w) {
+        if (wid == s_own) done = true;
+        if (done) {
+          if (lane == 0) __stcg(nrm_nxt + s_me, -1.0);
+        } else {
+          double2* a = W.Y64 + (size_t)s_me * Ma;
+          if (kap != 0.0) {
+            double sr = 0, si = 0;
+#pragma unroll
+            for (int k = 0; k < QRG_RC; ++k) {
+              const int r = j + lane + 32 * k;
+              if (r < Ma) {
+                const double2 u = hv[r];
+                sr = fma(u.x, c[k].x, fma(u.y, c[k].y, sr));
+                si = fma(u.x, c[k].y, fma(-u.y, c[k].x, si));
+              }
+            }
+            const double part = wsum2(sr, si, lane);
+            const double tr_ = kap * __shfl_sync(0xffffffffu, part, 0);
+            const double ti_ = kap * __shfl_sync(0xffffffffu, part, 16);
+#pragma unroll
+            for (int k = 0; k < QRG_RC; ++k) {
+              const int r = j + lane + 32 * k;
+              if (r < Ma) {
+                const double2 u = hv[r];
+                c[k].x -= u.x * tr_ - u.y * ti_;
+                c[k].y -= u.x * ti_ + u.y * tr_;
+                __stcg(a + r, c[k]);
+              }
+            }
+          }
+          // partial norm over rows > j: downdated, recomputed where that cancels
+          const double2 ajv = make_double2(__shfl_sync(0xffffffffu, c[0].x, 0), __shfl_sync(0xffffffffu, c[0].y, 0));
+          double nn = nrm_me - (ajv.x * ajv.x + ajv.y * ajv.y);
+          if (nn <= 1.4901161193847656e-8 * nref_me) {
+            double sq = 0;
+#pragma unroll
+            for (int k = 0; k < QRG_RC; ++k) {
+              const int r = j + lane + 32 * k;
+              if (r > j && r < Ma) sq += c[k].x * c[k].x + c[k].y * c[k].y;
+            }
+            nn = wsum(sq);
+            nref_me = nn;
+          }
+          nrm_me = nn;
+          if (lane == 0) __stcg(nrm_nxt + s_me, nn);
+          // registers move one row: lane l takes row j+1+l+32k
+#pragma unroll
+          for (int k = 0; k < QRG_RC; ++k) {
+            const double2 nxt = k + 1 < QRG_RC ? c[k + 1] : make_double2(0.0, 0.0);
+            const double2 own = c[k];
+            // lane l receives from lane l+1 its row j+1+l+32k; lane 31 receives lane 0's next row
+            const double xs = __shfl_sync(0xffffffffu, lane == 0 ? nxt.x : own.x, (lane + 1) & 31);
+            const double ys = __shfl_sync(0xffffffffu, lane == 0 ? nxt.y : own.y, (lane + 1) & 31);
+            c[k] = make_double2(xs, ys);
+          }
+        }
+      }
+      __syncthreads();                          // hv is rewritten by the next matrix
+    }
+    if (!grid_barrier(gs, status)) return;
+  }
+  // B = R^H: column c of B is row c of R, B[i, c] = conj(R[c, i]), R[c, qperm[i]] = X[c, qperm[i]]
+  if (have) {
+    const BondWork& W = work[w_me];
+    const int Na = s_off[w_me + 1] - s_off[w_me], Ma = Ma_me, cc = s_me;
+    for (int i = lane; i < Na; i += 32) {
+      double2 v = make_double2(0.0, 0.0);
+      if (cc < i) {
+        const double2 r = __ldcg(W.Y64 + cc + (size_t)__ldcg(W.qperm + i) * Ma);
+        v = make_double2(r.x, -r.y);
+      } else if (cc == i) {
+        const double2 b = __ldcg(W.V + cc);
+        v = make_double2(b.x, -b.y);
+      }
+      W.G64[i + (size_t)cc * Na] = v;
+    }
+  }
+}
+
 // B = R^H (Na x Na, col-major, lower triangular) from the upper triangle of the QR workspace
 __global__ void k_qrcp_rh(const BondWork* work, int n_work) {
   const int w = blockIdx.y;
@@ -490,6 +749,38 @@ int qrcp_smem_cluster(int m_cap, int n_cap) {
     cudaGetLastError();
   }
   return 0;
+}
+
+int qrcp_grid_ok() {
+  int a = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_qrcp_grid, QRG_THREADS, 32 * QRG_RC * sizeof(double2)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return a >= 1;
+}
+
+int qrcp_grid_fits(int n_work, int m_cap, int total_cols_cap, int blocks) {
+  return n_work <= QRG_MAX_ITEMS && m_cap <= 32 * QRG_RC && blocks > 0 &&
+         (total_cols_cap + blocks - 1) / blocks <= QRG_WARPS;
+}
+
+void launch_qrcp_grid(const BondWork* work, int n_work, int blocks, unsigned* sync3, int* status, cudaStream_t st) {
+  cudaMemsetAsync(sync3, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(sync3 + 2, 0, sizeof(unsigned), st);
+  GridSync gs{sync3, (int*)(sync3 + 2)};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks, 1, 1);
+  cfg.blockDim = dim3(QRG_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = 32 * QRG_RC * sizeof(double2);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_qrcp_grid, work, n_work, gs, status);
 }
 
 int qrcp_cluster_size(int want) {
