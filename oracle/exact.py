@@ -62,8 +62,10 @@ def full_liouvillian_run(ch, dt, K, ops):
     return np.array(out)
 
 
-def full_trotter_run(N, rho0, gates_q, gates_h, K, ops, insert=None):
-    """Same schedule as PT-TEBD (chain half O(dt/4) E(dt/2) O(dt/4), twice per step), no baths."""
+def full_trotter_run(N, rho0, gates_q, gates_h, K, ops, insert=None, insert_at=0):
+    """Same schedule as PT-TEBD (chain half O(dt/4) E(dt/2) O(dt/4), twice per step), no baths.
+
+    insert = (site, A, side) applies A. or .A on that site after step insert_at."""
     nb = N - 1
     Gq = [_embed_two_site(gates_q[b], b, N) for b in range(nb)]
     Gh = [_embed_two_site(gates_h[b], b, N) for b in range(nb)]
@@ -75,13 +77,18 @@ def full_trotter_run(N, rho0, gates_q, gates_h, K, ops, insert=None):
     for b in range(0, nb, 2):
         half = Gq[b] @ half
     v = _product_vector(rho0)
+    ins = None
     if insert is not None:
         n, A, side = insert
         S = model.left_superop(A) if side == "left" else model.right_superop(A)
-        v = np.kron(np.kron(np.eye(4 ** n), S), np.eye(4 ** (N - n - 1))) @ v
+        ins = np.kron(np.kron(np.eye(4 ** n), S), np.eye(4 ** (N - n - 1)))
+    if ins is not None and insert_at == 0:
+        v = ins @ v
     out = [_site_observables(v, N, ops)]
-    for _ in range(K):
+    for k in range(1, K + 1):
         v = half @ (half @ v)
+        if ins is not None and insert_at == k:
+            v = ins @ v
         out.append(_site_observables(v, N, ops))
     return np.array(out)
 

@@ -118,10 +118,12 @@ class RunResult:
 
 
 def simulate_chain(ci: ChainInputs, w, ops, K=None, variant="qr", normalize=False,
-                   insert=None, multiplet_tol=MULTIPLET_TOL, keep_lambdas=False):
+                   insert=None, multiplet_tol=MULTIPLET_TOL, keep_lambdas=False, insert_at=0):
     """Run the PT-TEBD schedule for one chain; observe every op on every site after each step.
 
-    insert = (site, 2x2 operator, 'left'|'right') applies that super-operator at t = 0 (App. A.4).
+    insert = (site, 2x2 operator, 'left'|'right') applies that super-operator to the full augmented
+    MPS after step insert_at (0: the initial state), before that step's readout (App. A.4; the
+    branching at a later time follows the two-time correlation procedure of App. B.2).
     """
     K = w.K if K is None else K
     m = ci.init_mps.copy() if ci.init_mps is not None else pttebd.product_state(ci.rho0)
@@ -131,7 +133,7 @@ def simulate_chain(ci: ChainInputs, w, ops, K=None, variant="qr", normalize=Fals
             site_caps.append(None)
         else:
             site_caps.append(pttebd.caps(ci.pt[n]))
-    if insert is not None:
+    if insert is not None and insert_at == 0:
         pttebd.apply_local(m, insert[0], insert[1], insert[2])
     opv = [model.op_vector(o) for o in ops]
 
@@ -143,6 +145,8 @@ def simulate_chain(ci: ChainInputs, w, ops, K=None, variant="qr", normalize=Fals
     obs.append(o); tr.append(t); chis.append(m.chis()); kaps.append(m.kappas()); lns.append(m.lognorm)
     for k in range(1, K + 1):
         pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps, variant, multiplet_tol)
+        if insert is not None and insert_at == k:
+            pttebd.apply_local(m, insert[0], insert[1], insert[2])
         o, t = pttebd.observe(m, caps_at(k), opv, normalize)
         obs.append(o); tr.append(t); chis.append(m.chis()); kaps.append(m.kappas()); lns.append(m.lognorm)
         if keep_lambdas:
