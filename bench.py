@@ -274,8 +274,8 @@ def run_ours(args, rank, world, local):
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp64_peak = SM_COUNT * FP64_FLOPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
     achieved = (fl_svd / K / n_layers) / (svd_ms / n_layers / 1e3) / 1e12
-    kernel = ("k_jacobi_grid<double> (FP64 one-sided Jacobi SVD)" if args.precision == "fp64" else
-              "bond SVD: k_jacobi_grid<float> sweeps + FP64 Newton-Schulz + k_jacobi_grid<double> polish")
+    kernel = ("bond SVD (FP64 in every mode): pivoted QR k_qrcp_grid, one-sided Jacobi on R^H "
+              "k_jacobi_grid<double>, U_D = D V_D / sigma k_mix_gemm")
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
                 "work": "Golub-Van Loan SVD flops 4(4m^2n+8mn^2+9n^3) x4 (complex) per bond update",

@@ -183,3 +183,25 @@ def test_standalone_svd_against_lapack():
             rec = (U[i] * s[i][None, :]) @ V[i].conj().T
             assert np.max(np.abs(rec - A[i])) < 1e-12 * ref[0] * max(m, n)
             assert np.max(np.abs(U[i].conj().T @ U[i] - np.eye(k))) < 1e-12 * max(m, n)
+
+
+@pytest.mark.parametrize("env", [{"PT_TEBD_QR": "cluster"}, {"PT_TEBD_QR": "global"},
+                                 {"PT_TEBD_PRECOND": "0"}, {"PT_TEBD_SVD": "mixed"}])
+def test_alternative_svd_routes(env, monkeypatch):
+    # every selectable bond-SVD route (pivoted QR in cluster shared memory or in global memory,
+    # the Jacobi on D without preconditioning, the mixed FP32/FP64 sweeps of the fast path) is
+    # held to the same bar as the default on an uncapped window (the engine reads them at init)
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    w = workload("xyz5_twobaths", K=12, chi_max=256)
+    cis = oprob.build_inputs(w)
+    if "PT_TEBD_SVD" in env:
+        # a fast-path route (TF32x3 theta): the fast path's bar, 1e-5 strict over the first 6
+        # steps and 1e-5 + 10 x the oracle's response to 1e-7 perturbations afterwards
+        _, obs, _ = run_gpu(w, cis, OPS, precision="tf32x3")
+        ref = run_oracle(w, cis, OPS)[0]
+        err = np.abs(obs[:, 0, :5, :] - ref.obs).max(axis=(1, 2))
+        bar = 1e-5 + 10.0 * oracle_envelope(w, cis[0], OPS, scale=1e-7)
+        assert np.max(err[:7]) < 1e-5 and np.all(err <= bar), (err, bar)
+    else:
+        _compare(w, cis)
