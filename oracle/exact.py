@@ -1,7 +1,7 @@
 """Exact references that pin the oracle (test infrastructure).
 
 * ``full_liouvillian_run``: rho(t) = expm(L_chain t) rho(0) with the whole 4^N x 4^N Liouvillian of
-  the closed chain (alpha = 0). PT-TEBD reduces to Liouville-space TEBD there (Sec. II.A), so it
+  the chain without baths (alpha = 0; GKSL terms included when the chain has them). PT-TEBD reduces to Liouville-space TEBD there (Sec. II.A), so it
   must match this up to its O(dt^2) Trotter error.
 * ``full_trotter_run``: the same gate sequence as PT-TEBD, each gate embedded as a full 4^N
   matrix: PT-TEBD without truncation must equal it to rounding.
@@ -49,9 +49,9 @@ def _site_observables(v, N, ops):
 
 def full_liouvillian_run(ch, dt, K, ops):
     """<O_n>(k dt), k = 0..K, from expm of the whole closed-chain Liouvillian."""
+    from . import gksl
     N = ch.N
-    H = model.chain_hamiltonian(ch.eps, ch.J)
-    L = model.group_sites(model.hamiltonian_liouvillian(H), N)
+    L = gksl.full_liouvillian(ch)           # Hamiltonian part, plus GKSL terms if the chain has any
     v0 = _product_vector([model.product_state_vector(c) for c in ch.init])
     step = sla.expm(L * dt)
     v = v0.copy()

@@ -16,7 +16,9 @@ from typing import List, Optional
 
 import numpy as np
 
-from . import model, tempo, pttebd
+import scipy.linalg as sla
+
+from . import gksl, model, tempo, pttebd
 from .truncation import MULTIPLET_TOL
 
 CACHE_DIR = os.environ.get("PT_TEBD_CACHE",
@@ -35,6 +37,11 @@ class ChainInputs:
 
 
 def chain_gates(ch, dt, check=True):
+    if ch.gksl or ch.drive is not None:
+        # time-local dissipation (App. A.1, Sec. III.A.3): gates of the non-Hermitian bond
+        # generators, by scipy's matrix exponential
+        Ls = gksl.bond_liouvillians(ch)
+        return ([sla.expm(L * (dt / 4)) for L in Ls], [sla.expm(L * (dt / 2)) for L in Ls])
     Kp = model.absorbed_bond_hamiltonians(ch.eps, ch.J)
     gq, gh = [], []
     for Kb in Kp:

@@ -6,5 +6,5 @@ functionals, no contractions. Both the FP64 oracle (``oracle/``) and the GPU pat
 (``paper_2201_05529_gb300``) build their own inputs from these descriptions.
 """
 from .configs import (  # noqa: F401
-    ChainSpec, BathSpec, Workload, workload, WORKLOAD_NAMES, BASE_SEED,
+    ChainSpec, BathSpec, DriveSpec, Workload, workload, WORKLOAD_NAMES, BASE_SEED,
 )

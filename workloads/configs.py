@@ -35,17 +35,31 @@ class BathSpec:
 
 
 @dataclass(frozen=True)
+class DriveSpec:
+    """Two-spin thermal driving of sites 0 and 1 (the comparison network of Sec. III.A.3): a
+    time-local generator that relaxes the pair to the Gibbs state of its own two-spin Hamiltonian
+    at temperature T, with jump rates of scale `rate`."""
+    T: float
+    rate: float
+
+
+@dataclass(frozen=True)
 class ChainSpec:
-    """One spin-1/2 chain: on-site fields, bond couplings, product initial state, baths."""
+    """One spin-1/2 chain: on-site fields, bond couplings, product initial state, baths, and
+    optional time-local dissipation (App. A.1's GKSL terms of the system Liouvillians)."""
     N: int
     eps: Tuple[float, ...]                         # coefficient of s^z on each site
     J: Tuple[Tuple[float, float, float], ...]      # (Jx, Jy, Jz) per bond, len N-1
     init: str                                      # 'u' / 'd' per site
     baths: Tuple[Optional[BathSpec], ...]          # per site, None = no bath
+    gksl: Tuple[Tuple[int, str, float], ...] = ()  # (site, 'minus'|'plus'|'z', rate): L = sqrt(rate) op
+    drive: Optional[DriveSpec] = None              # two-spin thermal driving of sites 0, 1
 
     def __post_init__(self):
         assert len(self.eps) == self.N and len(self.J) == self.N - 1
         assert len(self.init) == self.N and len(self.baths) == self.N
+        assert all(0 <= g[0] < self.N and g[1] in ("minus", "plus", "z") and g[2] >= 0 for g in self.gksl)
+        assert self.drive is None or self.N >= 2
 
 
 @dataclass
@@ -155,12 +169,33 @@ def _config5(N=32, chi=96, kappa=16, K=20):
                     notes="random Gaussian augmented MPS, random PT tensors and unitary gates")
 
 
+def _config_gksl():
+    # the five-site XYZ chain with on-site GKSL terms next to a bath: decay on site 1, dephasing on
+    # site 3, pumping on site 5 (which also carries the hot bath)
+    hot = BathSpec(alpha=0.16, omega_c=4.0, T=5.0)
+    ch = _xyz_chain(5, [None, None, None, None, hot], "ududu")
+    ch = replace(ch, gksl=((0, "minus", 0.2), (2, "z", 0.1), (4, "plus", 0.05)))
+    return Workload("xyz5_gksl", (ch,), dt=0.05, K=40, chi_max=64, eps=1e-10, kappa_max=16,
+                    notes="N=5 XYZ with on-site decay, dephasing and pumping, one bath")
+
+
+def _config_drive():
+    # Sec. III.A.3: two extra spins on the left of the five-site chain, driven towards the Gibbs
+    # state of their own Hamiltonian (T = 1.6, the single-bath temperature of Sec. III.A); no PT-MPO
+    ch = _xyz_chain(7, [None] * 7, "ududud" + "u", hz_site0=0.0)
+    ch = replace(ch, drive=DriveSpec(T=1.6, rate=1.0))
+    return Workload("xyz7_twospin_drive", (ch,), dt=0.05, K=40, chi_max=64, eps=1e-8, kappa_max=1,
+                    notes="two-spin GKSL driving of a five-site XYZ chain (comparison network)")
+
+
 _BUILDERS = {
     "xyz3_onebath": _config1,
     "xyz5_twobaths": _config2,
     "xy21_allbaths": _config3,
     "xyz_ensemble64": _config4,
     "random32_stress": _config5,
+    "xyz5_gksl": _config_gksl,
+    "xyz7_twospin_drive": _config_drive,
 }
 WORKLOAD_NAMES = tuple(_BUILDERS)
 
