@@ -5,7 +5,9 @@ with NumPy, independently of the test oracle, from the physics of a workload:
 
 * gates (App. A.1): K'_{n,n+1} absorbs the on-site terms (whole end-site terms on the end bonds,
   halves elsewhere); G(tau) = U (x) conj(U), U = exp(-i K' tau) from an eigendecomposition, in the
-  per-site grouped Liouville index (p_n, p_{n+1}), p = i*2 + j (row-major vectorisation).
+  per-site grouped Liouville index (p_n, p_{n+1}), p = i*2 + j (row-major vectorisation). With
+  time-local GKSL terms (or the two-spin driving of Sec. III.A.3) the bond generator is assembled
+  by applying it to each basis operator and G(tau) is its matrix exponential.
 * PT-MPOs for Gaussian baths coupled to s^z (App. B.1): the discretised influence functional with
   memory coefficients eta_D built from G(t) = int_0^t int_0^s C(u) du ds, compressed slot by slot
   into an MPO (relative SVD threshold eps_tempo, bond cap kappa_max), diagonal in (input, output),
@@ -68,7 +70,77 @@ def liouville_gate(U):
     return G
 
 
+_JUMP = {"minus": np.array([[0, 0], [1, 0]], dtype=complex), "plus": np.array([[0, 1], [0, 0]], dtype=complex),
+         "z": _SIG["z"]}
+
+
+def _grouped_superop(action):
+    """16x16 matrix, in the grouped two-site index (i1 j1, i2 j2), of a linear map on 4x4 two-site
+    operators X[(i1 i2), (j1 j2)], found by applying it to each basis operator."""
+    M = np.zeros((16, 16), dtype=complex)
+    for i1 in range(2):
+        for j1 in range(2):
+            for i2 in range(2):
+                for j2 in range(2):
+                    E = np.zeros((4, 4), dtype=complex)
+                    E[i1 * 2 + i2, j1 * 2 + j2] = 1.0
+                    Y = action(E)
+                    col = (i1 * 2 + j1) * 4 + (i2 * 2 + j2)
+                    for a1 in range(2):
+                        for b1 in range(2):
+                            for a2 in range(2):
+                                for b2 in range(2):
+                                    M[(a1 * 2 + b1) * 4 + (a2 * 2 + b2), col] = Y[a1 * 2 + a2, b1 * 2 + b2]
+    return M
+
+
+def _lindblad_term(L):
+    """X -> L X L^dag - (L^dag L X + X L^dag L) / 2 for a two-site operator L (4x4)."""
+    LdL = L.conj().T @ L
+    return lambda X: L @ X @ L.conj().T - 0.5 * (LdL @ X + X @ LdL)
+
+
+def _bond_generators(ch):
+    """Bond generators of App. A.1 with time-local dissipation: -i[K', .] plus the sites' GKSL
+    terms (whole on the chain's end sites, half elsewhere), plus the two-spin driving generator of
+    Sec. III.A.3 on the first bond (jumps between eigenstates of the pair's own Hamiltonian with
+    rates 1 / (1 + e^{(E_a - E_b)/T}), whose steady state is the pair's Gibbs state)."""
+    N = ch.N
+    Kps = _bond_hamiltonians(ch.eps, ch.J)
+    jumps = [[] for _ in range(N)]
+    for site, op, rate in ch.gksl:
+        jumps[site].append(np.sqrt(rate) * _JUMP[op])
+    gens = []
+    for b in range(N - 1):
+        wl = 1.0 if b == 0 else 0.5
+        wr = 1.0 if b == N - 2 else 0.5
+        terms = [(1.0, -1j, Kps[b])]
+        ops = [(wl, np.kron(L, _I2)) for L in jumps[b]] + [(wr, np.kron(_I2, L)) for L in jumps[b + 1]]
+        if b == 0 and ch.drive is not None:
+            HB = ch.eps[0] * np.kron(_S["z"], _I2) + ch.eps[1] * np.kron(_I2, _S["z"]) + \
+                sum(ch.J[0][g] * np.kron(_S[n], _S[n]) for g, n in enumerate("xyz"))
+            E, V = np.linalg.eigh(HB)
+            for a in range(4):
+                for c in range(4):
+                    if a != c:
+                        r = ch.drive.rate / (1.0 + np.exp((E[a] - E[c]) / ch.drive.T))
+                        ops.append((1.0, np.sqrt(r) * np.outer(V[:, a], V[:, c].conj())))
+        Kp = Kps[b]
+
+        def action(X, Kp=Kp, ops=ops):
+            Y = -1j * (Kp @ X - X @ Kp)
+            for wgt, L in ops:
+                Y = Y + wgt * _lindblad_term(L)(X)
+            return Y
+        gens.append(_grouped_superop(action))
+    return gens
+
+
 def chain_gates(ch, dt):
+    if ch.gksl or ch.drive is not None:
+        from scipy.linalg import expm
+        gens = _bond_generators(ch)
+        return (np.array([expm(Lg * (dt / 4)) for Lg in gens]), np.array([expm(Lg * (dt / 2)) for Lg in gens]))
     gq, gh = [], []
     for Kp in _bond_hamiltonians(ch.eps, ch.J):
         w, V = np.linalg.eigh(Kp)

@@ -13,7 +13,8 @@ from oracle import model, problem as oprob
 from paper_2201_05529_gb300 import problem as pp
 
 
-@pytest.mark.parametrize("name,K", [("xyz3_onebath", 20), ("xyz5_twobaths", 12)])
+@pytest.mark.parametrize("name,K", [("xyz3_onebath", 20), ("xyz5_twobaths", 12), ("xyz5_gksl", 12),
+                                    ("xyz7_twospin_drive", 12)])
 def test_library_builders_agree_with_the_oracle(name, K):
     w = workload(name, K=K)
     chains, mpos = pp.build_problem(w)
@@ -21,6 +22,8 @@ def test_library_builders_agree_with_the_oracle(name, K):
     assert np.max(np.abs(chains[0]["gates_q"] - np.array(ci.gates_q))) < 1e-14
     assert np.max(np.abs(chains[0]["gates_h"] - np.array(ci.gates_h))) < 1e-14
     assert np.max(np.abs(chains[0]["rho0"] - np.array(ci.rho0))) == 0.0
+    if not mpos:
+        return
     pts = [None if i < 0 else mpos[i] for i in chains[0]["ptmpo_id"]]
     lib_inputs = oprob.ChainInputs(ci.N, ci.rho0, ci.gates_q, ci.gates_h, pts)
     a = oprob.simulate_chain(ci, w, [model.SZ, model.SX])
