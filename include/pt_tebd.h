@@ -175,6 +175,16 @@ int pt_svd_f64(const double* A, int m, int n, int batch, double* sigma, double* 
 int pt_svd_f64_noalloc(const double* A, int m, int n, int batch, double* sigma, double* U, double* V,
                        int max_sweeps, void* cuda_stream);
 
+/* ---- diagnostic (the paper has no counterpart) ----
+ * Exercises the failure path of the bounded grid barrier used by the cooperative kernels (Jacobi
+ * rounds, pivoted-QR steps) without a GPU fault: one CTA per SM runs three barriers with a wait limit
+ * of limit_ms (0 < limit_ms <= 10000); withheld_block (-1: none) is a CTA that never arrives. With
+ * no CTA withheld the call returns PT_OK; with one withheld the others time out, record the
+ * timeout, raise the abort flag and return, and the call returns PT_ERR_DEVICE_TIMEOUT; in both
+ * cases the context stays usable. device_status (may be NULL) receives the device status bits.
+ * Uses static device variables only and synchronises the device. */
+int pt_selftest_grid_barrier(int withheld_block, double limit_ms, int* device_status);
+
 #ifdef __cplusplus
 }
 #endif

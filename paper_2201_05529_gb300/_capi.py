@@ -27,6 +27,7 @@ EXPORTS = [
     "pt_tebd_clone",
     "pt_tebd_sync", "pt_tebd_destroy", "pt_tebd_last_error", "pt_tebd_set_timing",
     "pt_tebd_get_timing", "pt_svd_scratch_bytes", "pt_svd_f64", "pt_svd_f64_noalloc",
+    "pt_selftest_grid_barrier",
 ]
 
 
@@ -98,6 +99,10 @@ lib.pt_svd_f64.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.
 lib.pt_svd_f64_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_int, C.c_void_p]
 NOALLOC_MAX_BYTES = 16 << 20     # PT_SVD_NOALLOC_MAX_BYTES
+
+
+lib.pt_selftest_grid_barrier.argtypes = [C.c_int, C.c_double, C.POINTER(C.c_int)]
+lib.pt_selftest_grid_barrier.restype = C.c_int
 
 
 def _check(rc, h=None):
@@ -323,3 +328,12 @@ def svd_f64_noalloc(A, sigma, U, V, max_sweeps=0, stream=None):
     rc = lib.pt_svd_f64_noalloc(C.c_void_p(A.data_ptr()), m, n, b, C.c_void_p(sigma.data_ptr()),
                                 C.c_void_p(U.data_ptr()), C.c_void_p(V.data_ptr()), int(max_sweeps), st)
     _check(rc, None)
+
+
+def selftest_grid_barrier(withheld_block=-1, limit_ms=1.0):
+    """pt_selftest_grid_barrier: run the cooperative kernels' bounded grid barrier with one CTA
+    withheld (-1: none) and a wait limit of limit_ms; returns (return code, device status bits)
+    without raising, PT_ERR_DEVICE_TIMEOUT being the expected code when a CTA is withheld."""
+    st = C.c_int(0)
+    rc = lib.pt_selftest_grid_barrier(int(withheld_block), float(limit_ms), C.byref(st))
+    return rc, st.value

@@ -9,6 +9,7 @@ constexpr long long GRID_WAIT_LIMIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 struct GridSync {
   unsigned* count;   // arrival counter, zeroed before each launch
   int* abort;        // raised by a CTA whose wait timed out; releases every other CTA
+  long long limit;   // wait limit in clock cycles (GRID_WAIT_LIMIT_CYCLES for the path's kernels)
 };
 
 // Returns false when aborted (timeout here or elsewhere). The arrival counter only grows:
@@ -29,7 +30,7 @@ __device__ __forceinline__ bool grid_barrier(const GridSync& gs, int* status) {
       if ((int)(*vc - target) >= 0) break;
       if ((it & 63) == 0) {
         if (*(volatile int*)gs.abort) { ok = 0; break; }
-        if (clock64() - t0 > GRID_WAIT_LIMIT_CYCLES) {
+        if (clock64() - t0 > gs.limit) {
           atomicOr(status, ST_TIMEOUT);
           atomicExch(gs.abort, 1);
           ok = 0;

@@ -451,7 +451,7 @@ void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sw
   // the barrier's arrival counter and the abort flag start at zero for every launch
   cudaMemsetAsync(sync3, 0, sizeof(unsigned), st);
   cudaMemsetAsync(sync3 + 2, 0, sizeof(unsigned), st);
-  GridSync gs{sync3, (int*)(sync3 + 2)};
+  GridSync gs{sync3, (int*)(sync3 + 2), GRID_WAIT_LIMIT_CYCLES};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks, 1, 1);
   cfg.blockDim = dim3(GRID_THREADS, 1, 1);

@@ -769,7 +769,7 @@ int qrcp_grid_fits(int n_work, int m_cap, int total_cols_cap, int blocks) {
 void launch_qrcp_grid(const BondWork* work, int n_work, int blocks, unsigned* sync3, int* status, cudaStream_t st) {
   cudaMemsetAsync(sync3, 0, sizeof(unsigned), st);
   cudaMemsetAsync(sync3 + 2, 0, sizeof(unsigned), st);
-  GridSync gs{sync3, (int*)(sync3 + 2)};
+  GridSync gs{sync3, (int*)(sync3 + 2), GRID_WAIT_LIMIT_CYCLES};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks, 1, 1);
   cfg.blockDim = dim3(QRG_THREADS, 1, 1);
