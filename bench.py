@@ -133,7 +133,7 @@ def svd_flops(m, n):
 def step_flops(chis, kaps, N):
     """Algorithmic flops of one step: 3 bond updates per bond (the O layers twice, E once, per
     half step -> odd bonds 4x, even bonds 2x), each QR + theta + SVD + recovery, plus the PT layer."""
-    svd = other = 0.0
+    svd = other = theta = 0.0
     for b, (mL, nL, mR, nR, rL, rR, chc) in enumerate(bond_sizes(chis, kaps, N)):
         reps = 4 if b % 2 == 0 else 2
         mD, nD = 4 * rL, 4 * rR
@@ -144,7 +144,8 @@ def step_flops(chis, kaps, N):
         f_rec = 8.0 * (mL * rL * 4 * chc if mL > nL else 0) + 8.0 * (nR * rR * 4 * chc if nR > mR else 0)
         svd += reps * f_svd
         other += reps * (f_qr + f_theta + f_rec)
-    return svd, other
+        theta += reps * f_theta
+    return svd, other, theta
 
 
 # ------------------------------------------------------------------------ replicas across ranks
@@ -235,12 +236,13 @@ def run_ours(args, rank, world, local):
     sweeps = eng.get_svd_sweeps()
     hist_fast, _ = eng.read_history(W, K + 1)
     eng.destroy()
-    fl_svd = fl_other = 0.0
+    fl_svd = fl_other = fl_theta = 0.0
     for per_chain in dims:
         for c, (chi, kap) in enumerate(per_chain):
-            s_, o_ = step_flops(list(chi), list(kap), chains[c]["N"])
+            s_, o_, t_ = step_flops(list(chi), list(kap), chains[c]["N"])
             fl_svd += s_
             fl_other += o_
+            fl_theta += t_
 
     # --- the plain FP64 GPU path on the same window (for the FP32-TC vs FP64 comparison)
     fp64 = None
@@ -279,17 +281,32 @@ def run_ours(args, rank, world, local):
     achieved = (fl_svd / K / n_layers) / (svd_ms / n_layers / 1e3) / 1e12
     kernel = ("bond SVD (FP64 in every mode): pivoted QR k_qrcp_grid, one-sided Jacobi on R^H "
               "k_jacobi_grid<double>, U_D = D V_D / sigma k_mix_gemm")
+    mp = measured_peaks()
+    src = ("MEASURED_PEAKS.json gives HBM copy and bf16 GEMM peaks only" if mp else "MEASURED_PEAKS.json absent")
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
                 "work": "Golub-Van Loan SVD flops 4(4m^2n+8mn^2+9n^3) x4 (complex) per bond update",
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x median SM clock (of derived; "
-                               "MEASURED_PEAKS.json absent; a DFMA probe measured 1.20 TFLOP/s)",
+                               + src + "; a DFMA probe measured 1.20 TFLOP/s)",
                 "svd_ms_per_launch": svd_ms / n_layers,
                 "svd_sweeps_last_step": {"fp64": [int(x) for x in sweeps[:, 0]],
                                          "fp32": [int(x) for x in sweeps[:, 1]]},
                 "stage_ms_per_step": {"site": stage[0], "blocks_qr": stage[1], "theta": stage[2],
                                       "svd_fp64": stage[3], "svd_fp32": stage[7], "svd_precond": stage[8],
                                       "truncate": stage[4], "recover": stage[5], "readout": stage[6]}}
+
+    if args.precision != "fp64" and stage[2] > 0:
+        # the tcgen05 theta GEMM against the TF32 (or bf16) tensor peak: measured bf16 x the nominal
+        # dense ratio (TF32 1.1 / bf16 2.25 PFLOP/s), or the fallback figure without the file
+        bf16 = float(mp["bf16_tflops"]) if mp and "bf16_tflops" in mp else 1900.0
+        tpeak = bf16 * (1.1 / 2.25) if args.precision in ("tf32x3", "tf32x1") else bf16
+        tach = (fl_theta / K) / (stage[2] / 1e3) / 1e12
+        roofline["theta_tensor"] = {
+            "kernel": "k_tc_pack + k_tc_theta (tcgen05 3M complex GEMM, split pieces)", "bound": "tensor",
+            "achieved": tach, "peak": tpeak, "unit": "TFLOP/s", "frac": tach / tpeak,
+            "work": "128 r^2 chi + 2048 r^2 per bond update (algorithmic, complex MAC = 8)",
+            "peak_source": ("of measured: bf16 GEMM burst x 1.1/2.25" if mp else "of fallback: 1.9 PF bf16 x 1.1/2.25")
+            if args.precision in ("tf32x3", "tf32x1") else ("of measured: bf16 GEMM burst" if mp else "of fallback")}
 
     # --- end to end through the C ABI: host inputs -> init (H2D) -> W+K steps -> history (D2H)
     torch.cuda.synchronize()
