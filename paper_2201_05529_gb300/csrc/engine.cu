@@ -81,7 +81,7 @@ struct pt_tebd {
   int grid_blocks = 0;                // whole-GPU Jacobi: CTAs per launch (0: use the cluster kernel)
   int rt_odd = 1, rt_even = 1, kc_odd = 1, kc_even = 1;   // fast path: theta tile / K-chunk caps
   std::vector<int*> bond_info;        // per bond (odd list, then even list): its info words
-  bool mixed_svd = true;              // fast path: FP32 bulk sweeps + FP64 polish (PT_TEBD_SVD=fp64 disables)
+  bool mixed_svd = false;             // fast path: FP32 bulk sweeps + FP64 polish on D (PT_TEBD_SVD=mixed)
   bool precond = true;                // QR-preconditioned Jacobi (PT_TEBD_PRECOND=0 disables)
   int qr_cluster = 1;
   int qr_smem_cluster = 0;            // >0: the pivoted QR runs in cluster shared memory

@@ -54,7 +54,8 @@ void launch_qrcp_precondition(const BondWork* work, int n_work, int cluster, int
 void launch_qrcp_finish(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st);
 void launch_mix_gemm_av(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st);
 
-// fast path: FP32 bulk sweeps + FP64 Newton-Schulz re-orthonormalisation + FP64 polish (mixed_svd.cu)
+// optional fast-path SVD on D (PT_TEBD_SVD=mixed): FP32 bulk sweeps + FP64 Newton-Schulz
+// re-orthonormalisation + FP64 polish (mixed_svd.cu)
 void launch_mixed_fp32(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,
                        int* status, cudaStream_t st);
 void launch_mixed_reorth(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st);
