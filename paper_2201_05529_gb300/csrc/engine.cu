@@ -697,7 +697,8 @@ int build(pt_tebd* h) {
     const char* pc = getenv("PT_TEBD_PRECOND");
     h->precond = !(pc && std::string(pc) == "0");
     int k = std::max(h->kcap_odd, h->kcap_even);
-    h->qr_cluster = ptk::qrcp_cluster_size(std::max(1, std::min(16, (k + 31) / 32)));
+    h->qr_cluster = ptk::qrcp_cluster_size(std::max(1, std::min(16, (k + 31) / 32)),
+                                           std::max(h->mcap_odd, h->mcap_even), k);
     const char* qv = getenv("PT_TEBD_QR");
     if (!(qv && std::string(qv) == "global"))
       h->qr_smem_cluster = ptk::qrcp_smem_cluster(std::max(h->mcap_odd, h->mcap_even), k);

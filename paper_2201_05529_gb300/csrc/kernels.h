@@ -43,7 +43,7 @@ void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sw
 
 // QR preconditioning of the bond SVD (qrcp.cu): pivoted QR of D into Y64, B = R^H into G64;
 // after the Jacobi on B: V_D = P U', U_D = D V_D / sigma
-int qrcp_cluster_size(int want);
+int qrcp_cluster_size(int want, int m_cap, int n_cap);
 int qrcp_smem_cluster(int m_cap, int n_cap);
 // whole-GPU variant (cooperative, one CTA per SM): usable when qrcp_grid_ok() and the layer fits
 int qrcp_grid_ok();

@@ -1,17 +1,17 @@
 // QR-preconditioned one-sided Jacobi for the bond SVD (App. A.2 (f-g)).
 //
-// A one-sided Jacobi on a rank-deficient, strongly graded D needs many sweeps (26-32 on the
+// A one-sided Jacobi on a rank-deficient, strongly graded D needs many sweeps (17-23 on the
 // five-site chain's 256x256 blocks); after a column-pivoted QR, D P = Q R, the same Jacobi on R^H
-// converges in ~9 (Drmac and Veselic's preconditioning). Here:
-//   1. k_qrcp: Householder QR with column pivoting of a copy of D, one thread-block cluster per
-//      matrix (column swaps and trailing updates spread over its CTAs, cluster barriers between
-//      the steps; exact trailing column norms recomputed at every step for the pivot choice);
-//   2. k_qrcp_rh: B = R^H (lower triangular, Na x Na);
-//   3. the grid Jacobi on B gives B = U' S V'^H, i.e. R = V' S U'^H and D = (Q V') S (P U')^H;
-//   4. k_qrcp_vd: V_D = P U' (rows permuted back);
-//   5. U_D = D V_D S^{-1} by an FP64 GEMM (k_mix_gemm op 2) and a column scaling. Its error in
-//      column c is ~eps ||D|| / s_c, and that column enters the truncated state scaled by s_c, so
-//      the state error stays at rounding level; Q is never formed.
+// converges in ~8 (Drmac and Veselic's preconditioning). Here:
+//   1. the pivoted Householder QR of D, with B = R^H written directly: on the whole GPU
+//      (k_qrcp_grid) where a layer's columns fit one per warp, else one thread-block cluster per
+//      matrix with the columns in shared memory or, for large matrices, in global memory
+//      (k_qrcp_cl);
+//   2. the grid Jacobi on B gives B = U' S V'^H, i.e. R = V' S U'^H and D = (Q V') S (P U')^H;
+//   3. k_qrcp_vd: V_D = P U' (rows permuted back);
+//   4. U_D = D V_D S^{-1} by an FP64 GEMM (k_mix_gemm op 2) and a column scaling (k_qrcp_ud). Its
+//      error in column c is ~eps ||D|| / s_c, and that column enters the truncated state scaled by
+//      s_c, so the state error stays at rounding level; Q is never formed.
 #include <cooperative_groups.h>
 
 #include "grid_sync.cuh"
@@ -48,167 +48,25 @@ __device__ __forceinline__ double wsum2(double a, double b, int lane) {
 
 }  // namespace
 
-// Column-pivoted Householder QR in place on X (Ma x Na col-major, Ma >= Na); X's upper triangle
-// becomes R; qperm[k] = original column of position k; nrm: Na doubles of scratch.
-__global__ void __launch_bounds__(1024) k_qrcp(const BondWork* work, int n_work) {
-  cg::cluster_group cl = cg::this_cluster();
-  const int w = blockIdx.x / cl.num_blocks();
-  if (w >= n_work) return;
-  const BondWork& W = work[w];
-  int Ma, Na;
-  shape(W, &Ma, &Na);
-  if (Na <= 0) return;
-  double2* X = W.Y64;
-  double* nrm = W.aux;
-  int* qperm = W.qperm;
-  const int rank = (int)cl.block_rank(), ncta = (int)cl.num_blocks();
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwb = blockDim.x >> 5;
-  const int gw = wid * ncta + rank, ngw = ncta * nwb;
-  const int gt = rank * blockDim.x + tid, ngt = ncta * blockDim.x;
-  __shared__ double s_red[32];
-  __shared__ int s_piv;
-  // copy D into the workspace, initial column norms, identity permutation
-  for (size_t i = gt; i < (size_t)Ma * Na; i += ngt) X[i] = W.A[i];
-  for (int k = gt; k < Na; k += ngt) __stcg(qperm + k, k);
-  cl.sync();
-  for (int k = gw; k < Na; k += ngw) {
-    double s = 0;
-    for (int r = lane; r < Ma; r += 32) {
-      const double2 x = __ldcg(X + (size_t)k * Ma + r);
-      s += x.x * x.x + x.y * x.y;
-    }
-    s = wsum(s);
-    if (lane == 0) __stcg(nrm + k, s);
-  }
-  cl.sync();
-  for (int j = 0; j < Na && j < Ma; ++j) {
-    // pivot: the remaining column of largest norm (every CTA scans the same values in the same order)
-    if (wid == 0) {
-      double best = -1.0;
-      int bi = j;
-      for (int k = j + lane; k < Na; k += 32) {
-        const double v = __ldcg(nrm + k);
-        if (v > best || (v == best && k < bi)) { best = v; bi = k; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) s_piv = bi;
-    }
-    __syncthreads();
-    const int p = s_piv;
-    if (p != j) {
-      double2* cj = X + (size_t)j * Ma;
-      double2* cp = X + (size_t)p * Ma;
-      for (int r = gt; r < Ma; r += ngt) {
-        const double2 a = __ldcg(cj + r), b = __ldcg(cp + r);
-        __stcg(cj + r, b);
-        __stcg(cp + r, a);
-      }
-      cl.sync();                                  // all reads of the old columns done
-      if (gt == 0) {
-        const double t = __ldcg(nrm + j);
-        __stcg(nrm + j, __ldcg(nrm + p));
-        __stcg(nrm + p, t);
-        const int q = __ldcg(qperm + j);
-        __stcg(qperm + j, __ldcg(qperm + p));
-        __stcg(qperm + p, q);
-      }
-    }
-    cl.sync();
-    // Householder vector of column j (rows j..Ma-1): every CTA computes the same scalars
-    const double2* x = X + (size_t)j * Ma;
-    double part = 0;
-    for (int r = j + tid; r < Ma; r += blockDim.x) {
-      const double2 v = __ldcg(x + r);
-      part += v.x * v.x + v.y * v.y;
-    }
-    part = wsum(part);
-    if (lane == 0) s_red[wid] = part;
-    __syncthreads();
-    if (wid == 0) {
-      double t = lane < nwb ? s_red[lane] : 0.0;
-      t = wsum(t);
-      if (lane == 0) s_red[0] = t;
-    }
-    __syncthreads();
-    const double nrm2 = s_red[0];
-    __syncthreads();
-    const double2 alpha = __ldcg(x + j);
-    const double aabs = sqrt(alpha.x * alpha.x + alpha.y * alpha.y), xn = sqrt(nrm2);
-    double tau = 0.0;
-    double2 ph = make_double2(1.0, 0.0), beta = alpha, ujinv = make_double2(0.0, 0.0);
-    if (xn > 0.0) {
-      if (aabs > 0.0) ph = make_double2(alpha.x / aabs, alpha.y / aabs);
-      beta = make_double2(-ph.x * xn, -ph.y * xn);
-      const double2 uj = make_double2(ph.x * (aabs + xn), ph.y * (aabs + xn));   // alpha - beta
-      const double uj2 = uj.x * uj.x + uj.y * uj.y;
-      tau = 2.0 * uj2 / (nrm2 - aabs * aabs + uj2);
-      ujinv = make_double2(uj.x / uj2, -uj.y / uj2);                             // 1 / u_j
-    }
-    // trailing columns: a <- a - tau u (u^H a) with u = x / u_j (u_j = 1); then new partial norms
-    if (tau != 0.0) {
-      for (int k = j + 1 + gw; k < Na; k += ngw) {
-        double2* a = X + (size_t)k * Ma;
-        double sr = 0, si = 0;
-        for (int r = j + lane; r < Ma; r += 32) {
-          double2 u = make_double2(1.0, 0.0);
-          if (r != j) {
-            const double2 xv = __ldcg(x + r);
-            u = make_double2(xv.x * ujinv.x - xv.y * ujinv.y, xv.x * ujinv.y + xv.y * ujinv.x);
-          }
-          const double2 av = __ldcg(a + r);
-          sr += u.x * av.x + u.y * av.y;      // conj(u) a
-          si += u.x * av.y - u.y * av.x;
-        }
-        sr = wsum(sr);
-        si = wsum(si);
-        const double tr_ = tau * sr, ti_ = tau * si;
-        double nn = 0;
-        for (int r = j + lane; r < Ma; r += 32) {
-          double2 u = make_double2(1.0, 0.0);
-          if (r != j) {
-            const double2 xv = __ldcg(x + r);
-            u = make_double2(xv.x * ujinv.x - xv.y * ujinv.y, xv.x * ujinv.y + xv.y * ujinv.x);
-          }
-          double2 av = __ldcg(a + r);
-          av.x -= u.x * tr_ - u.y * ti_;
-          av.y -= u.x * ti_ + u.y * tr_;
-          __stcg(a + r, av);
-          if (r > j) nn += av.x * av.x + av.y * av.y;
-        }
-        nn = wsum(nn);
-        if (lane == 0) __stcg(nrm + k, nn);
-      }
-    }
-    cl.sync();                                    // every warp has read column j
-    if (gt == 0) {
-      __stcg(X + (size_t)j * Ma + j, beta);
-      __stcg(nrm + j, 0.0);
-    }
-    cl.sync();
-  }
-}
-
 constexpr int QR_SMEM_THREADS = 512;
 
-// The same factorisation with the matrix held in the shared memory of a thread-block cluster.
-// Storage column s lives in CTA s % C at local index s / C. Pivoting is logical: the pivot column
-// is not moved; it is marked done and its position recorded (qp[j] = p), so R[i, j] is row i of
+// The same factorisation with one thread-block cluster per matrix. Storage column s belongs to CTA
+// s % C at local index s / C; GL = false keeps the columns in the CTAs' shared memory (pivot columns
+// read through distributed shared memory), GL = true leaves them in the workspace Y64 (global,
+// through L2) for matrices too large for shared memory. Pivoting is logical: the pivot column is
+// not moved; it is marked done and its position recorded (qp[j] = p), so R[i, j] is row i of
 // storage column qp[j] (i < j) and R[j, j] = beta of that column. Each step needs one cluster
 // barrier: every CTA publishes its best remaining column (a double-buffered candidate), reads the
-// C candidates and the pivot column (distributed shared memory), and updates its own columns.
-// At the end every CTA writes the rows of B = R^H that belong to its columns.
+// C candidates and the pivot column, and updates its own columns. At the end every CTA writes the
+// rows of B = R^H that belong to its columns.
 // The partial column norms that pick the pivots are downdated, n <- n - |a_j|^2, and recomputed
 // where that cancels below sqrt(eps) of the last exact value (the safeguard of LAPACK's pivoted
 // QR); they only choose pivots. The reflector uses the exact norm of the pivot column.
-// Dynamic shared memory: X[lq_cap][m_cap] | hv[m_cap] | beta[lq_cap] (double2), nrm[lq_cap] |
-// nref[lq_cap] (double), qp[n_cap] | pos[n_cap] | done[lq_cap] (int).
+// Dynamic shared memory: [X[lq_cap][m_cap] if !GL] | hv[m_cap] | beta[lq_cap] (double2),
+// nrm[lq_cap] | nref[lq_cap] (double), qp[n_cap] | pos[n_cap] | done[lq_cap] (int).
+template <bool GL>
 __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
-    k_qrcp_smem(const BondWork* work, int n_work, int lq_cap, int m_cap, int n_cap, int* status) {
+    k_qrcp_cl(const BondWork* work, int n_work, int lq_cap, int m_cap, int n_cap, int* status) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int w = blockIdx.x / C;
@@ -222,8 +80,8 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
     return;
   }
   extern __shared__ double2 sm[];
-  double2* X = sm;
-  double2* hv = X + (size_t)lq_cap * m_cap;
+  double2* X = sm;                                // local columns (shared memory mode only)
+  double2* hv = GL ? sm : X + (size_t)lq_cap * m_cap;
   double2* betaL = hv + m_cap;
   double* nrm = (double*)(betaL + lq_cap);
   double* nref = nrm + lq_cap;
@@ -237,16 +95,28 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
   __shared__ int s_p;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int Ln = rank < Na ? (Na - rank + C - 1) / C : 0;
+  // local column l, its element loads and stores (L2-coherent in global mode)
+  auto colp = [&](int l) -> double2* {
+    return GL ? W.Y64 + (size_t)(rank + l * C) * Ma : X + (size_t)l * m_cap;
+  };
+  auto ld = [&](const double2* q) -> double2 { return GL ? __ldcg(q) : *q; };
+  auto st = [&](double2* q, double2 v) {
+    if (GL) __stcg(q, v);
+    else *q = v;
+  };
   // load the own columns, their norms
   for (int e = tid; e < Ln * Ma; e += blockDim.x) {
     const int l = e / Ma, r = e % Ma;
-    X[(size_t)l * m_cap + r] = W.A[r + (size_t)(rank + l * C) * Ma];
+    st(colp(l) + r, W.A[r + (size_t)(rank + l * C) * Ma]);
   }
   __syncthreads();
   for (int l = wid; l < Ln; l += nw) {
-    const double2* a = X + (size_t)l * m_cap;
+    const double2* a = colp(l);
     double sq = 0;
-    for (int r = lane; r < Ma; r += 32) sq += a[r].x * a[r].x + a[r].y * a[r].y;
+    for (int r = lane; r < Ma; r += 32) {
+      const double2 v = ld(a + r);
+      sq += v.x * v.x + v.y * v.y;
+    }
     sq = wsum(sq);
     if (lane == 0) {
       nrm[l] = sq;
@@ -296,13 +166,15 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
     }
     __syncthreads();
     const int p = s_p, owner = p % C, lp = p / C;
-    const double2* src = cl.map_shared_rank(X, owner) + (size_t)lp * m_cap;
+    const double2* src;
+    if constexpr (GL) src = W.Y64 + (size_t)p * Ma;
+    else src = cl.map_shared_rank(X, owner) + (size_t)lp * m_cap;
     // 2. the pivot column (rows j..) and its exact squared norm: every CTA sums the same values
     //    in the same order, then derives the Householder scalars with identical arithmetic
     {
       double part = 0;
       for (int r = j + tid; r < Ma; r += blockDim.x) {
-        const double2 xv = src[r];
+        const double2 xv = ld(src + r);
         hv[r] = xv;
         part += xv.x * xv.x + xv.y * xv.y;
       }
@@ -344,11 +216,11 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
     // 3. own remaining columns: a <- a - kappa v (v^H a); partial norms over rows > j
     for (int l = wid; l < Ln; l += nw) {
       if (done[l]) continue;
-      double2* a = X + (size_t)l * m_cap;
+      double2* a = colp(l);
       if (kap != 0.0) {
         double sr = 0, si = 0;
         for (int r = j + lane; r < Ma; r += 32) {
-          const double2 u = hv[r], av = a[r];
+          const double2 u = hv[r], av = ld(a + r);
           sr = fma(u.x, av.x, fma(u.y, av.y, sr));
           si = fma(u.x, av.y, fma(-u.y, av.x, si));
         }
@@ -356,18 +228,21 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
         const double tr_ = kap * __shfl_sync(0xffffffffu, part, 0), ti_ = kap * __shfl_sync(0xffffffffu, part, 16);
         for (int r = j + lane; r < Ma; r += 32) {
           const double2 u = hv[r];
-          double2 av = a[r];
+          double2 av = ld(a + r);
           av.x -= u.x * tr_ - u.y * ti_;
           av.y -= u.x * ti_ + u.y * tr_;
-          a[r] = av;
+          st(a + r, av);
         }
         __syncwarp();
       }
-      const double2 ajv = a[j];
+      const double2 ajv = ld(a + j);
       double nn = nrm[l] - (ajv.x * ajv.x + ajv.y * ajv.y);
       if (nn <= 1.4901161193847656e-8 * nref[l]) {     // cancellation: recompute
         double sq = 0;
-        for (int r = j + 1 + lane; r < Ma; r += 32) sq += a[r].x * a[r].x + a[r].y * a[r].y;
+        for (int r = j + 1 + lane; r < Ma; r += 32) {
+          const double2 v = ld(a + r);
+          sq += v.x * v.x + v.y * v.y;
+        }
         nn = wsum(sq);
         if (lane == 0) nref[l] = nn;
       }
@@ -384,10 +259,13 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
   __syncthreads();
   for (int l = wid; l < Ln; l += nw) {
     const int s = rank + l * C, i = pos[s];
-    const double2* a = X + (size_t)l * m_cap;
+    const double2* a = colp(l);
     for (int c = lane; c < Na; c += 32) {
       double2 v = make_double2(0.0, 0.0);           // B[i, c] = conj(R[c, i])
-      if (c < i) v = make_double2(a[c].x, -a[c].y);
+      if (c < i) {
+        const double2 x = ld(a + c);
+        v = make_double2(x.x, -x.y);
+      }
       else if (c == i) v = make_double2(betaL[l].x, -betaL[l].y);
       W.G64[i + (size_t)c * Na] = v;
     }
@@ -653,25 +531,6 @@ __global__ void __launch_bounds__(QRG_THREADS, 1)
   }
 }
 
-// B = R^H (Na x Na, col-major, lower triangular) from the upper triangle of the QR workspace
-__global__ void k_qrcp_rh(const BondWork* work, int n_work) {
-  const int w = blockIdx.y;
-  if (w >= n_work) return;
-  const BondWork& W = work[w];
-  int Ma, Na;
-  shape(W, &Ma, &Na);
-  const size_t tot = (size_t)Na * Na;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % Na), c = (int)(idx / Na);     // B[i, c] = conj(R[c, i]) for c <= i
-    double2 v = make_double2(0.0, 0.0);
-    if (c <= i) {
-      const double2 r = W.Y64[c + (size_t)i * Ma];
-      v = make_double2(r.x, -r.y);
-    }
-    W.G64[idx] = v;
-  }
-}
-
 // V_D = P U': V[qperm[k], c] = U'[k, c] (U' = the normalised columns of B after the Jacobi)
 __global__ void k_qrcp_vd(const BondWork* work, int n_work) {
   const int w = blockIdx.y;
@@ -705,7 +564,7 @@ __global__ void k_qrcp_ud(const BondWork* work, int n_work) {
 static cudaLaunchConfig_t qr_cfg(int n_work, int cluster, cudaStream_t st, cudaLaunchAttribute* at) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(n_work * cluster, 1, 1);
-  cfg.blockDim = dim3(1024, 1, 1);
+  cfg.blockDim = dim3(QR_SMEM_THREADS, 1, 1);
   cfg.stream = st;
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = cluster;
@@ -716,40 +575,41 @@ static cudaLaunchConfig_t qr_cfg(int n_work, int cluster, cudaStream_t st, cudaL
   return cfg;
 }
 
-static size_t qr_smem_bytes(int lq, int m_cap, int n_cap) {
-  return sizeof(double2) * ((size_t)lq * m_cap + m_cap + lq) + sizeof(double) * 2 * lq +
+static size_t qr_smem_bytes(int lq, int m_cap, int n_cap, bool gl) {
+  return sizeof(double2) * ((gl ? 0 : (size_t)lq * m_cap) + m_cap + lq) + sizeof(double) * 2 * lq +
          sizeof(int) * (2 * (size_t)n_cap + lq);
 }
 
-// Cluster size for the shared-memory factorisation of matrices up to m_cap x n_cap; 0 if they do
-// not fit (the global-memory kernel is used then).
-int qrcp_smem_cluster(int m_cap, int n_cap) {
-  cudaFuncSetAttribute(k_qrcp_smem, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  for (int c = 16; c >= 2; c >>= 1) {
+// Largest cluster (16, 8, ... down to `lowest`) for which the factorisation of matrices up to
+// m_cap x n_cap fits (shared memory per CTA, co-scheduling); 0 if none does.
+template <bool GL>
+static int qr_pick_cluster(int m_cap, int n_cap, int want, int lowest) {
+  cudaFuncSetAttribute(k_qrcp_cl<GL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int c = 16; c >= lowest; c >>= 1) {
+    if (c > want) continue;
     const int lq = (n_cap + c - 1) / c;
-    const size_t bytes = qr_smem_bytes(lq, m_cap, n_cap);
-    if (bytes > 200 * 1024) return 0;
-    if (cudaFuncSetAttribute(k_qrcp_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+    const size_t bytes = qr_smem_bytes(lq, m_cap, n_cap, GL);
+    if (bytes > 200 * 1024) {
+      if (GL) return 0;
+      continue;
+    }
+    if (cudaFuncSetAttribute(k_qrcp_cl<GL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     cudaLaunchAttribute at[1];
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(c, 1, 1);
-    cfg.blockDim = dim3(QR_SMEM_THREADS, 1, 1);
+    cudaLaunchConfig_t cfg = qr_cfg(1, c, 0, at);
     cfg.dynamicSmemBytes = bytes;
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = c;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_qrcp_smem, &cfg) == cudaSuccess && n > 0) return c;
+    if (cudaOccupancyMaxActiveClusters(&n, k_qrcp_cl<GL>, &cfg) == cudaSuccess && n > 0) return c;
     cudaGetLastError();
   }
   return 0;
 }
+
+// Cluster size for the shared-memory factorisation of matrices up to m_cap x n_cap; 0 if they do
+// not fit (the columns then stay in global memory).
+int qrcp_smem_cluster(int m_cap, int n_cap) { return qr_pick_cluster<false>(m_cap, n_cap, 16, 2); }
 
 int qrcp_grid_ok() {
   int a = 0;
@@ -783,33 +643,22 @@ void launch_qrcp_grid(const BondWork* work, int n_work, int blocks, unsigned* sy
   cudaLaunchKernelEx(&cfg, k_qrcp_grid, work, n_work, gs, status);
 }
 
-int qrcp_cluster_size(int want) {
-  cudaFuncSetAttribute(k_qrcp, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  for (int c = 16; c >= 1; c >>= 1) {
-    if (c > want) continue;
-    cudaLaunchAttribute at[1];
-    cudaLaunchConfig_t cfg = qr_cfg(1, c, 0, at);
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_qrcp, &cfg) == cudaSuccess && n > 0) return c;
-    cudaGetLastError();
-  }
-  return 1;
+// Cluster size for the global-memory variant (at most `want` CTAs per matrix; 1 at the least).
+int qrcp_cluster_size(int want, int m_cap, int n_cap) {
+  const int c = qr_pick_cluster<true>(m_cap, n_cap, want, 1);
+  return c > 0 ? c : 1;
 }
 
 void launch_qrcp_precondition(const BondWork* work, int n_work, int cluster, int smem_cluster, int k_cap, int m_cap,
                               int* status, cudaStream_t st) {
   cudaLaunchAttribute at[1];
-  if (smem_cluster > 0) {
-    const int lq = (k_cap + smem_cluster - 1) / smem_cluster;
-    cudaLaunchConfig_t cfg = qr_cfg(n_work, smem_cluster, st, at);
-    cfg.blockDim = dim3(QR_SMEM_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = qr_smem_bytes(lq, m_cap, k_cap);
-    cudaLaunchKernelEx(&cfg, k_qrcp_smem, work, n_work, lq, m_cap, k_cap, status);
-    return;
-  }
-  cudaLaunchConfig_t cfg = qr_cfg(n_work, cluster, st, at);
-  cudaLaunchKernelEx(&cfg, k_qrcp, work, n_work);
-  k_qrcp_rh<<<dim3(128, n_work), 256, 0, st>>>(work, n_work);
+  const bool gl = smem_cluster <= 0;
+  const int c = gl ? cluster : smem_cluster;
+  const int lq = (k_cap + c - 1) / c;
+  cudaLaunchConfig_t cfg = qr_cfg(n_work, c, st, at);
+  cfg.dynamicSmemBytes = qr_smem_bytes(lq, m_cap, k_cap, gl);
+  if (gl) cudaLaunchKernelEx(&cfg, k_qrcp_cl<true>, work, n_work, lq, m_cap, k_cap, status);
+  else cudaLaunchKernelEx(&cfg, k_qrcp_cl<false>, work, n_work, lq, m_cap, k_cap, status);
 }
 
 void launch_qrcp_finish(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st) {
