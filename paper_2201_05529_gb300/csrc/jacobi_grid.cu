@@ -13,6 +13,8 @@
 //
 // on_b: the matrix is the square R^H left by the pivoted QR (qrcp.cu); only its left vectors are
 // wanted there, so the right factor is not accumulated.
+#include <climits>
+
 #include "grid_sync.cuh"
 #include "kernels.h"
 
@@ -80,7 +82,7 @@ template <typename R>
 __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R>::T* V, double* nrm, int Ma,
                                              int Na, int i, int j, double fro, double floor_eps, int grp, int gw,
                                              int lane, R (*s_part)[GROUP_WARPS][4], R (*s_rot)[8], int* cnt_slot,
-                                             bool with_v) {
+                                             bool with_v, int* stamp, int g_round, int skip_before) {
   using C2 = typename Cx<R>::T;
   const R eps = Cx<R>::EPS;
   if (i > j) { const int tt = i; i = j; j = tt; }
@@ -101,6 +103,7 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
   // Ma <= RC * 128); the rest, if any, are read again
   constexpr int RC = 2, STEP = 32 * GROUP_WARPS;
   C2 xs[RC], ys[RC];
+  const int si = __ldcg(stamp + i), sj = __ldcg(stamp + j);
   {
     R gr = 0, gi = 0;
 #pragma unroll
@@ -118,6 +121,9 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
       gr = fma(x.x, y.x, fma(x.y, y.y, gr));
       gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
     }
+    // unchanged pair: neither column has rotated since this pair was checked one sweep ago (and
+    // found orthogonal, or it would carry that round's stamp), so gamma would come out the same
+    if (max(si, sj) < skip_before) return;       // uniform: every lane read the same stamps
     const R part = wsum2(gr, gi, lane);
     if (lane == 0) s_part[grp][gw][0] = part;
     if (lane == 16) s_part[grp][gw][1] = part;
@@ -154,6 +160,8 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
       const R cg_ = c * ig;
       cer = cg_ * gr;
       cei = -cg_ * gi;
+      __stcg(stamp + i, g_round);
+      __stcg(stamp + j, g_round);
       const R tg = sgn * g2 * sgm * sgm * q, al2 = al - tg, be2 = be + tg;
       if (al2 >= R(0.25) * al && be2 >= R(0.25) * be) {
         flag = 1;
@@ -283,6 +291,7 @@ __global__ void __launch_bounds__(GRID_THREADS)
         cnt[2 * w] = 0;
         cnt[2 * w + 1] = 0;
       }
+      for (int c = gt; c < Na; c += ngt) __stcg(work[w].perm + c, -1);   // rotation stamps (perm is free until the end)
     }
     const int gwarp = wid * gridDim.x + blockIdx.x, ngwarp = gridDim.x * (blockDim.x / 32);
     int base = 0;
@@ -314,6 +323,14 @@ __global__ void __launch_bounds__(GRID_THREADS)
   int sweep = 0;
   bool any = false;
   for (int w = 0; w < n_work; ++w) any |= s_active[w] != 0;
+  // fixed stride of the global round index (every matrix's tournament fits in it), so that a pair
+  // that meets in round r of every sweep met one stride earlier, whichever matrices are still active
+  int stride = 1;
+  for (int w = 0; w < n_work; ++w)
+    if (s_Na[w] >= 2) {
+      const int nb = (s_Na[w] + 1) / 2, nbp = nb + (nb & 1);
+      stride = max(stride, nbp - 1);
+    }
   while (any && sweep < max_sweeps) {
     const int par = sweep & 1;
     if (blockIdx.x == 0)
@@ -328,6 +345,7 @@ __global__ void __launch_bounds__(GRID_THREADS)
         rounds = max(rounds, nbp - 1);
       }
     for (int round = 0; round < rounds; ++round) {
+      const int g_round = sweep * stride + round;    // a pair meets in the same round of every sweep
       if (tid == 0) {
         int o = 0;
         for (int w = 0; w < n_work; ++w) {
@@ -361,7 +379,8 @@ __global__ void __launch_bounds__(GRID_THREADS)
           else if (sr == 1) { i = i0 + sub; j = j0 + 1 - sub; }
           else { i = sub == 0 ? i0 : j0; j = i + 1; }          // pairs inside each block
           process_pair<R>(s_A[w], s_V[w], work[w].aux, Ma, Na, i, j, s_fro[w], floor_eps, grp, gw, lane, s_part,
-                          s_rot, &cnt[2 * w + par], !on_b);
+                          s_rot, &cnt[2 * w + par], !on_b, work[w].perm, g_round,
+                          sweep > 0 ? g_round - stride : INT_MIN);
           named_sync(9 + slot, 32 * GROUP_WARPS * 2);
         }
       }
