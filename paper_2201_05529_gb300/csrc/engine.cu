@@ -105,6 +105,9 @@ struct pt_tebd {
   double2* d_tr_now = nullptr;
   double2* d_Lbuf = nullptr;
   double2* d_Rbuf = nullptr;
+  double2* d_Mbuf = nullptr;          // readout: site tensors with the augmented leg closed
+  size_t* d_moff = nullptr;           // [n_sites] offsets into d_Mbuf
+  int gx_m = 1;
   int ld = 1;
   static constexpr int MAX_OPS = 16;
 
@@ -277,9 +280,11 @@ void enqueue_observe_history(pt_tebd* h) {
   if (h->n_ops == 0) return;
   cudaEvent_t e = nullptr;
   ev_begin(h, 6, &e);
+  ptk::k_observe_m<<<dim3(h->gx_m, h->n_chains, h->n_max), 256, 0, h->stream>>>(h->T, h->n_chains, h->d_Mbuf,
+                                                                                  h->d_moff);
   ptk::k_observe<<<h->n_chains, 256, 0, h->stream>>>(h->T, h->n_chains, h->d_ops, h->n_ops, h->n_max,
                                                      h->d_hist, h->d_hist_tr, h->d_Lbuf, h->d_Rbuf,
-                                                     h->ld, 1);
+                                                     h->ld, 1, h->d_Mbuf, h->d_moff);
   ev_end(h, e);
 }
 
@@ -755,6 +760,23 @@ int build(pt_tebd* h) {
   h->hist_cap = h->K_limit + 1;
   if (!h->d_Lbuf || !h->d_Rbuf || !h->d_ops_now || !h->d_obs_now || !h->d_tr_now)
     return h->fail(PT_ERR_OOM, "readout buffers");
+  {
+    // M_n capacity per site: chi_l,cap x 4 x chi_r,cap (the augmented leg is closed)
+    std::vector<size_t> moff(h->n_sites, 0);
+    size_t tot = 0, mx = 1;
+    for (int c = 0; c < C; ++c)
+      for (int n = 0; n < h->chains[c].N; ++n) {
+        const int s = h->site0[c] + n, B = h->lam0[c] + n;
+        const size_t cap = (size_t)h->lam_cap_h[B] * 4 * h->lam_cap_h[B + 1];
+        moff[s] = tot;
+        tot += cap;
+        mx = std::max(mx, cap);
+      }
+    h->d_Mbuf = (double2*)h->dalloc(sizeof(double2) * std::max<size_t>(1, tot));
+    h->d_moff = upload(h, moff);
+    if (!h->d_Mbuf || !h->d_moff) return h->fail(PT_ERR_OOM, "readout buffers");
+    h->gx_m = (int)std::min<size_t>(64, (mx + 255) / 256);
+  }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "init");
   return check_cuda(h, "init");
 }
@@ -884,9 +906,11 @@ int pt_tebd_observe(pt_tebd_t h, const double* ops, int n_ops, double* out, doub
   std::vector<cplx> v;
   op_vectors(ops, n_ops, v);
   if (n_ops > 0) cudaMemcpyAsync(h->d_ops_now, v.data(), sizeof(cplx) * v.size(), cudaMemcpyHostToDevice, h->stream);
+  ptk::k_observe_m<<<dim3(h->gx_m, h->n_chains, h->n_max), 256, 0, h->stream>>>(h->T, h->n_chains, h->d_Mbuf,
+                                                                                  h->d_moff);
   ptk::k_observe<<<h->n_chains, 256, 0, h->stream>>>(h->T, h->n_chains, h->d_ops_now, n_ops, h->n_max,
                                                      h->d_obs_now, h->d_tr_now, h->d_Lbuf, h->d_Rbuf,
-                                                     h->ld, 0);
+                                                     h->ld, 0, h->d_Mbuf, h->d_moff);
   int rc = check_cuda(h, "observe");
   if (rc != PT_OK) return rc;
   const size_t n = (size_t)h->n_chains * h->n_max * n_ops;

@@ -17,9 +17,10 @@ __global__ void k_truncate(Tables T, const BondWork* work, int n_work, int chi_m
                            double mtol);
 __global__ void k_recover(Tables T, const BondWork* work, int n_work);
 __global__ void k_caps(Tables T, int n_mpos);
+__global__ void k_observe_m(Tables T, int n_chains, double2* Mbuf, const size_t* moff);
 __global__ void k_observe(Tables T, int n_chains, const double2* ops, int n_ops, int n_max,
                           double2* obs, double2* trace, double2* Lbuf, double2* Rbuf, int ld,
-                          int use_history);
+                          int use_history, const double2* Mbuf, const size_t* moff);
 __global__ void k_step_inc(int* step);
 __global__ void k_svd_load(const double2* A, int m, int n, int batch, double2* work_A,
                            size_t strideA);

@@ -482,9 +482,35 @@ __global__ void k_caps(Tables T, int n_mpos) {
 // Contract each augmented leg with its cap C^(k), close Liouville legs with vec(I) except
 // vec(O^T) on the measured site, including the lambdas (App. A.3); one block per chain.
 // Writes obs[c][n][j] (complex, raw Tr(O rho) times exp(lognorm)) and trace[c].
+// M_n[l][p][r] = sum_a Gamma_n[l,p,a,r] C_n^(k)[a]: each site tensor with its augmented leg
+// closed by the current cap (App. A.3), for every site of every chain in one launch
+// (grid: x over elements, y over chains, z over sites), so that the readout passes below work on
+// the small M_n instead of contracting the kappa leg again in each pass.
+__global__ void k_observe_m(Tables T, int n_chains, double2* Mbuf, const size_t* moff) {
+  const int c = blockIdx.y, n = blockIdx.z;
+  if (c >= n_chains || n >= T.chain_N[c]) return;
+  const int k = *T.step;
+  const int s = T.chain_site0[c] + n, B = T.chain_lam0[c] + n;
+  const int chl = T.lam_chi[B], chr = T.lam_chi[B + 1], kap = T.site_kappa[s];
+  const double2* G = T.site_gam[s];
+  const int m = T.site_mpo[s];
+  const double2* capv = m >= 0 ? T.mpo_cap[T.mpo_cap_off[m] + k] : nullptr;
+  double2* M = Mbuf + moff[s];
+  const size_t tot = (size_t)chl * 4 * chr;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % chr);
+    const size_t t = idx / chr;
+    const int p = (int)(t % 4), l = (int)(t / 4);
+    double2 v = cmk(0, 0);
+    for (int a = 0; a < kap; ++a) v = cfma(G[gidx(l, p, a, r, kap, chr)], capv ? capv[a] : cmk(1, 0), v);
+    M[idx] = v;
+  }
+}
+
 __global__ void k_observe(Tables T, int n_chains, const double2* ops, int n_ops, int n_max,
                           double2* obs, double2* trace, double2* Lbuf, double2* Rbuf, int ld,
-                          int use_history) {
+                          int use_history, const double2* Mbuf, const size_t* moff) {
   const int c = blockIdx.x;
   if (c >= n_chains) return;
   __shared__ double red[32];
@@ -496,26 +522,20 @@ __global__ void k_observe(Tables T, int n_chains, const double2* ops, int n_ops,
     obs += (size_t)k * n_chains * n_max * n_ops;
     trace += (size_t)k * n_chains;
   }
-  auto cap = [&](int n, int a) -> double2 {
-    const int m = T.site_mpo[s0 + n];
-    if (m < 0) return cmk(1, 0);
-    return T.mpo_cap[T.mpo_cap_off[m] + k][a];
+  // M_n[l][p][r] (k_observe_m) at index (l * 4 + p) * chr + r
+  auto Mel = [&](int n, int l, int p, int r, int chr) -> double2 {
+    return Mbuf[moff[s0 + n] + ((size_t)l * 4 + p) * chr + r];
   };
   // left prefix: Lp[0] = lambda_0; Lp[n+1][r] = lambda_{n+1}[r] sum_l Lp[n][l] V_n[l][r]
   if (threadIdx.x == 0) Lp[0] = cmk(T.lam_ptr[B0][0], 0);
   __syncthreads();
   for (int n = 0; n < N; ++n) {
-    const int chl = T.lam_chi[B0 + n], chr = T.lam_chi[B0 + n + 1], kap = T.site_kappa[s0 + n];
-    const double2* G = T.site_gam[s0 + n];
+    const int chl = T.lam_chi[B0 + n], chr = T.lam_chi[B0 + n + 1];
     const double* lr = T.lam_ptr[B0 + n + 1];
     for (int r = threadIdx.x; r < chr; r += blockDim.x) {
       double2 acc = cmk(0, 0);
       for (int l = 0; l < chl; ++l) {
-        double2 v = cmk(0, 0);
-        for (int a = 0; a < kap; ++a) {
-          const double2 g = cadd(G[gidx(l, 0, a, r, kap, chr)], G[gidx(l, 3, a, r, kap, chr)]);
-          v = cfma(g, cap(n, a), v);
-        }
+        const double2 v = cadd(Mel(n, l, 0, r, chr), Mel(n, l, 3, r, chr));   // trace of the site
         acc = cfma(Lp[(size_t)n * ld + l], v, acc);
       }
       Lp[(size_t)(n + 1) * ld + r] = cscale(acc, lr[r]);
@@ -526,17 +546,12 @@ __global__ void k_observe(Tables T, int n_chains, const double2* ops, int n_ops,
   if (threadIdx.x == 0) Rs[(size_t)N * ld] = cmk(1, 0);
   __syncthreads();
   for (int n = N - 1; n >= 0; --n) {
-    const int chl = T.lam_chi[B0 + n], chr = T.lam_chi[B0 + n + 1], kap = T.site_kappa[s0 + n];
-    const double2* G = T.site_gam[s0 + n];
+    const int chl = T.lam_chi[B0 + n], chr = T.lam_chi[B0 + n + 1];
     const double* lr = T.lam_ptr[B0 + n + 1];
     for (int l = threadIdx.x; l < chl; l += blockDim.x) {
       double2 acc = cmk(0, 0);
       for (int r = 0; r < chr; ++r) {
-        double2 v = cmk(0, 0);
-        for (int a = 0; a < kap; ++a) {
-          const double2 g = cadd(G[gidx(l, 0, a, r, kap, chr)], G[gidx(l, 3, a, r, kap, chr)]);
-          v = cfma(g, cap(n, a), v);
-        }
+        const double2 v = cadd(Mel(n, l, 0, r, chr), Mel(n, l, 3, r, chr));
         acc = cfma(v, cscale(Rs[(size_t)(n + 1) * ld + r], lr[r]), acc);
       }
       Rs[(size_t)n * ld + l] = acc;
@@ -550,8 +565,7 @@ __global__ void k_observe(Tables T, int n_chains, const double2* ops, int n_ops,
   if (threadIdx.x == 0) trace[c] = cscale(Lp[(size_t)N * ld], scale);
   // per site and op
   for (int n = 0; n < N; ++n) {
-    const int chl = T.lam_chi[B0 + n], chr = T.lam_chi[B0 + n + 1], kap = T.site_kappa[s0 + n];
-    const double2* G = T.site_gam[s0 + n];
+    const int chl = T.lam_chi[B0 + n], chr = T.lam_chi[B0 + n + 1];
     const double* lr = T.lam_ptr[B0 + n + 1];
     for (int j = 0; j < n_ops; ++j) {
       const double2* o = ops + j * 4;
@@ -559,12 +573,8 @@ __global__ void k_observe(Tables T, int n_chains, const double2* ops, int n_ops,
       for (size_t idx = threadIdx.x; idx < (size_t)chl * chr; idx += blockDim.x) {
         const int l = (int)(idx / chr), r = (int)(idx % chr);
         double2 v = cmk(0, 0);
-        for (int a = 0; a < kap; ++a) {
-          double2 g = cmk(0, 0);
 #pragma unroll
-          for (int p = 0; p < 4; ++p) g = cfma(o[p], G[gidx(l, p, a, r, kap, chr)], g);
-          v = cfma(g, cap(n, a), v);
-        }
+        for (int p = 0; p < 4; ++p) v = cfma(o[p], Mel(n, l, p, r, chr), v);
         const double2 left = Lp[(size_t)n * ld + l];
         const double2 right = cscale(Rs[(size_t)(n + 1) * ld + r], lr[r]);
         part = cfma(cmul(left, v), right, part);
