@@ -30,6 +30,7 @@ METRIC = "PT-TEBD site-steps/s and TFLOP/s vs roofline, FP32-TC vs FP64 at <=1e-
 UNIT = "site-steps/s"
 DEFAULT_WORKLOAD = "xyz5_twobaths"
 SM_COUNT = 152
+JACOBI_DRAM_BYTES_PER_LAUNCH = 1378048 + 174848   # bytes, ncu capture of the current k_jacobi_grid
 FP64_FLOPS_PER_CLK_PER_SM = 4.0       # 2 DFMA / clk / SM: 1.25 TFLOP/s nominal at 2.07 GHz x 152 SMs
 
 
@@ -284,7 +285,12 @@ def run_ours(args, rank, world, local):
     mp = measured_peaks()
     src = ("MEASURED_PEAKS.json gives HBM copy and bf16 GEMM peaks only" if mp else "MEASURED_PEAKS.json absent")
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                # DRAM read + write of one k_jacobi_grid launch on a full-size layer (step 16, two
+                # 256x256 bonds) from an ncu capture of this kernel version (profiles/)
+                "traffic": JACOBI_DRAM_BYTES_PER_LAUNCH,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one k_jacobi_grid launch "
+                                  "at step 16 (full-size layer); the matrices stay in L2 otherwise",
                 "work": "Golub-Van Loan SVD flops 4(4m^2n+8mn^2+9n^3) x4 (complex) per bond update",
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x median SM clock (of derived; "
                                + src + "; a DFMA probe measured 1.20 TFLOP/s)",
