@@ -85,3 +85,23 @@ def test_product_fft_spectra_equal_the_definition():
     ok = np.isfinite(To) & (np.abs(Co / So) > 1e-6)
     assert ok.sum() > 10
     assert np.allclose(T[sel][ok], To[ok], rtol=1e-8, atol=0)
+
+
+def test_thermalised_chain_satisfies_the_fdt_at_the_bath_temperature():
+    # Sec. III.A.2: a chain thermalised by one bath obeys S / chi'' = coth(w / 2T), i.e. a flat
+    # effective temperature T(w) = T. Two-site XYZ chain, bath (alpha = 0.32, wc = 4, T = 1.6) on
+    # site 1, branched at t_ss = 10 (App. B.2) and propagated to tau_max = 10; the finite tau_max
+    # leaves a ripple, so the band average is held to 5 % and every point to 25 %
+    from workloads.configs import BathSpec
+    b = BathSpec(alpha=0.32, omega_c=4.0, T=1.6)
+    ch = ChainSpec(N=2, eps=(0.5, 0.0), J=((1.3, 0.7, 1.2),), init="ud", baths=(b, None))
+    dt, kss, ntau = 0.1, 100, 100
+    w = Workload("t", (ch,), dt=dt, K=kss + ntau, chi_max=64, eps=1e-10, kappa_max=32, eps_tempo=1e-7)
+    ci = problem.build_inputs(w)[0]
+    r = problem.simulate_chain(ci, w, [model.SZ], insert=(1, model.SZ, "left"), insert_at=kss)
+    C = r.obs[kss:, 1, 0]
+    om = np.linspace(0.4, 1.6, 7)
+    S, chi2, T = spectra.spectra(C, dt, om)
+    assert np.all(S > 0) and np.all(chi2 > 0)
+    assert abs(np.mean(T) - b.T) < 0.05 * b.T
+    assert np.max(np.abs(T - b.T)) < 0.25 * b.T
