@@ -49,9 +49,16 @@ typedef struct pt_tebd* pt_tebd_t;
 
 typedef enum {
   PT_FP64 = 0,      /* every stage in FP64 */
-  PT_TF32X3 = 1,    /* contractions in split TF32 on tensor cores, FP32 accumulate; FP64 SVD */
-  PT_BF16X3 = 2,    /* contractions in split BF16 on tensor cores, FP32 accumulate; FP64 SVD */
-  PT_TF32X1 = 3     /* single TF32 products (speed reference only) */
+  PT_TF32X3 = 1,    /* theta and the gate as one tensor-core GEMM (the gate folded into the right
+                       operand in FP64): each FP64 operand split into three TF32 pieces, the six
+                       piece products of order <= 2 accumulated in FP32 (limited by that
+                       accumulation to ~1e-6 relative); FP64 SVD, truncation and readout */
+  PT_BF16X3 = 2,    /* the same with three BF16 pieces (~24 significant bits) */
+  PT_TF32X1 = 3,    /* one TF32 piece, one product (speed reference only) */
+  PT_BF16_OZAKI = 4 /* the theta contraction from fixed-point BF16 slices: each operand row scaled by
+                       a power of two and cut into five slices, so the leading slice products sum
+                       exactly in the tensor cores' FP32 accumulators (Ozaki's error-free splitting);
+                       ~1e-9 relative to the rows' scale; FP64 SVD, truncation and readout */
 } pt_precision;
 
 /* One chain (App. A.1). Sites without a bath have ptmpo_id = -1 (augmented leg of dimension 1).
@@ -95,7 +102,10 @@ typedef void (*pt_free_fn)(void* ptr, void* ctx);
 void pt_tebd_set_allocator(pt_alloc_fn alloc, pt_free_fn free_fn, void* ctx);
 
 /* Build a handle: copies the chains, gates and PT-MPOs to the device, builds the caps (App. A.3)
- * on the device, and prepares the step. cuda_stream is a cudaStream_t (NULL: default stream). */
+ * on the device, and prepares the step. cuda_stream is a cudaStream_t (NULL: default stream).
+ * Errors: PT_ERR_ARG (malformed descriptors), PT_ERR_CAPACITY (an initial augmented MPS with a bond
+ * above chi_max, or a bond block beyond the kernels' limits), PT_ERR_OOM (the allocator returned
+ * NULL; everything allocated so far is released), PT_ERR_CUDA. */
 int pt_tebd_init(pt_tebd_t* out, const pt_chain_desc* chains, int n_chains,
                  const pt_mpo_desc* pt_mpos, int n_mpos, const pt_options* opt, void* cuda_stream);
 
@@ -167,10 +177,11 @@ int pt_svd_f64(const double* A, int m, int n, int batch, double* sigma, double* 
  * scratch pointer: the workspace is a static device array of PT_SVD_NOALLOC_MAX_BYTES bytes that
  * every GPU which loads this library holds until the process exits. A problem whose workspace
  * (pt_svd_scratch_bytes(m, n, batch)) is larger is rejected with PT_ERR_CAPACITY. The first call on
- * a device looks up the array's device address with that device current; make that first call
- * before any stream capture. All calls share the one array: calls that overlap on the GPU race and
- * corrupt each other, so the caller must serialise them. Each call clears what must start at zero
- * and synchronises the stream before returning. Messages: pt_tebd_last_error(NULL). */
+ * a device looks up the array's device address with that device current and caches it per device
+ * index (a cudaDeviceReset invalidates it). All calls share the one array: calls that overlap on the
+ * GPU race and corrupt each other, so the caller must serialise them. Each call clears what must
+ * start at zero, reads the status word back and synchronises the stream before returning, so it
+ * must not be called while that stream is being captured. Messages: pt_tebd_last_error(NULL). */
 #define PT_SVD_NOALLOC_MAX_BYTES ((size_t)16 << 20)
 int pt_svd_f64_noalloc(const double* A, int m, int n, int batch, double* sigma, double* U, double* V,
                        int max_sweeps, void* cuda_stream);

@@ -5,7 +5,7 @@ to check against it by eye: Liouville-space conventions (Sec. II.A, App. A.1), t
 second-order Trotter schedule (Eq. (propagator-env), App. A.1), the bath correlation
 function (App. B.1), the discretised influence functional and its PT-MPO compression
 (App. B.1, following the PT-TEMPO literature the paper cites), the augmented-MPS bond
-update (App. A.2, sequence (c-h)), the PT-MPO site contraction (App. A.2, (i-j)), cap
+update (App. A.2), the PT-MPO site contraction (App. A.2), cap
 tensors (App. A.3) and readout, including two-time correlations (App. A.4).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference leg of

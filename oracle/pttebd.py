@@ -7,16 +7,16 @@ plus a scalar log-norm: the true state is exp(lognorm) times the network (Liouvi
 2-norms are not conserved, so lambda is kept at unit 2-norm and the factor carried separately).
 Sites are 0-based here: site i sits between bonds i and i+1.
 
-Bond update (App. A.2, sequence (c-h)), for sites (i, i+1) and a two-site gate G:
-  (c-d) B_L = lambda_i Gamma_i   as a matrix [(l, a), (p, c)],
-        B_R = Gamma_{i+1} lambda_{i+2} as a matrix [(c, q), (b, r)];
-  (d-e) the paper reduces B_L, B_R by truncated SVDs; the QR variant replaces them by exact
-        QR / LQ reductions B_L = Q_L R_L, B_R = L_R Q_R (no truncation). Both are implemented;
-  (e-f) D = R_L lambda_{i+1} G L_R, i.e. D[(u,p'),(q',v)] = sum G[p'q',pq] R_L[u,p,c] lam_c L_R[c,q,v];
-  (f-g) truncated SVD of D with the relative rule of App. A.2; the kept singular values,
-        normalised, become lambda_{i+1} and their norm goes into the log-norm;
-  (g-h) Gamma_i = lambda_i^{-1} Q_L U,  Gamma_{i+1} = V^dagger Q_R lambda_{i+2}^{-1}.
-Site contraction (App. A.2, (i-j)): Gamma'[l,p',b,r] = sum_{a,p} Gamma[l,p,a,r] P[a,p,p',b].
+Bond update (App. A.2), for sites (i, i+1) and a two-site gate G, in four moves:
+  reduce   -- the outer blocks B_L = lambda_i Gamma_i (rows (l, a), columns (p, c)) and
+              B_R = Gamma_{i+1} lambda_{i+2} (rows (c, q), columns (b, r)) are reduced exactly by
+              QR and LQ, B_L = Q_L R_L, B_R = L_R Q_R (the paper reduces them by truncated SVDs;
+              both variants are implemented and agree without truncation);
+  contract -- D[(u,p'),(q',v)] = sum G[p'q',pq] R_L[u,p,c] lambda_{i+1,c} L_R[c,q,v];
+  split    -- truncated SVD of D with the paper's relative rule; the kept singular values,
+              normalised, become lambda_{i+1}, their norm goes into the log-norm;
+  recover  -- Gamma_i = lambda_i^{-1} Q_L U and Gamma_{i+1} = V^dagger Q_R lambda_{i+2}^{-1}.
+Site contraction (App. A.2): Gamma'[l,p',b,r] = sum_{a,p} Gamma[l,p,a,r] P[a,p,p',b].
 Caps (App. A.3): C^(K) = 1, C^(k-1)[a] = sum_{i,o,b} P^(k)[a,i,o,b] (iota_i/d) tau_o C^(k)[b].
 Readout: contract each augmented leg with its cap, close Liouville legs with vec(I) (trace) or
 vec(O^T) (observable), including the lambdas; observables are raw Tr(O rho) unless normalised.
@@ -81,7 +81,7 @@ def _reduce_qr(BL, BR):
 
 
 def _reduce_svd(BL, BR, eps):
-    """The paper's (d-e): truncated SVDs U_L (S_L V_L^dag) and (U_R S_R) V_R^dag of B_L and B_R."""
+    """The paper's reduction: truncated SVDs U_L (S_L V_L^dag) and (U_R S_R) V_R^dag of B_L and B_R."""
     u, s, vh = np.linalg.svd(BL, full_matrices=False)
     c = truncation_rank(s, eps, len(s))
     QL, RL = u[:, :c], s[:c, None] * vh[:c]
@@ -98,10 +98,9 @@ def bond_update(m: AugmentedMPS, i: int, G: np.ndarray, chi_max: int, eps: float
     lamL, lamC, lamR = m.lam[i], m.lam[i + 1], m.lam[i + 2]
     chl, _, kl, chc = GL.shape
     _, _, kr, chr_ = GR.shape
-    # (c-d)
+    # reduce: the outer blocks
     BL = (lamL[:, None, None, None] * GL).transpose(0, 2, 1, 3).reshape(chl * kl, 4 * chc)
     BR = (GR * lamR[None, None, None, :]).reshape(chc * 4, kr * chr_)
-    # (d-e)
     if variant == "qr":
         QL, RL, LR, QR = _reduce_qr(BL, BR)
     elif variant == "svd":
@@ -109,11 +108,11 @@ def bond_update(m: AugmentedMPS, i: int, G: np.ndarray, chi_max: int, eps: float
     else:
         raise ValueError(variant)
     rL, rR = RL.shape[0], LR.shape[1]
-    # (e-f)
+    # contract: theta and the gate
     theta = np.einsum("upc,c,cqv->upqv", RL.reshape(rL, 4, chc), lamC, LR.reshape(chc, 4, rR))
     theta = np.einsum("PQpq,upqv->uPQv", np.asarray(G).reshape(4, 4, 4, 4), theta)
     Dm = theta.reshape(rL * 4, 4 * rR)
-    # (f-g)
+    # split: truncated SVD
     try:
         U, S, Vh = np.linalg.svd(Dm, full_matrices=False)
     except np.linalg.LinAlgError:                       # zgesdd failure: fall back to zgesvd
@@ -126,7 +125,7 @@ def bond_update(m: AugmentedMPS, i: int, G: np.ndarray, chi_max: int, eps: float
     m.lam[i + 1] = S / nrm
     m.lognorm += np.log(nrm)
     m.trunc_log.append((i, chi, disc))
-    # (g-h)
+    # recover the site tensors
     newL = (QL @ U.reshape(rL, 4 * chi)).reshape(chl, kl, 4, chi).transpose(0, 2, 1, 3)
     m.gam[i] = newL / lamL[:, None, None, None]
     newR = (Vh.reshape(chi * 4, rR) @ QR).reshape(chi, 4, kr, chr_)
@@ -135,7 +134,7 @@ def bond_update(m: AugmentedMPS, i: int, G: np.ndarray, chi_max: int, eps: float
 
 
 def site_contract(m: AugmentedMPS, i: int, P: np.ndarray):
-    """(i-j): Gamma'[l,p',b,r] = sum_{a,p} Gamma[l,p,a,r] P[a,p,p',b]."""
+    """PT site contraction (App. A.2): Gamma'[l,p',b,r] = sum_{a,p} Gamma[l,p,a,r] P[a,p,p',b]."""
     m.gam[i] = np.einsum("lpar,apqb->lqbr", m.gam[i], P)
 
 

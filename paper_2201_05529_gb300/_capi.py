@@ -15,8 +15,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpttebd.so")
 
-PT_FP64, PT_TF32X3, PT_BF16X3, PT_TF32X1 = 0, 1, 2, 3
-PRECISIONS = {"fp64": PT_FP64, "tf32x3": PT_TF32X3, "bf16x3": PT_BF16X3, "tf32x1": PT_TF32X1}
+PT_FP64, PT_TF32X3, PT_BF16X3, PT_TF32X1, PT_BF16_OZAKI = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": PT_FP64, "tf32x3": PT_TF32X3, "bf16x3": PT_BF16X3, "tf32x1": PT_TF32X1,
+              "bf16_ozaki": PT_BF16_OZAKI}
 ERRORS = {-1: "PT_ERR_ARG", -2: "PT_ERR_OOM", -3: "PT_ERR_CAPACITY", -4: "PT_ERR_SVD_NOCONV",
           -5: "PT_ERR_DEVICE_TIMEOUT", -6: "PT_ERR_NAN", -7: "PT_ERR_CUDA", -8: "PT_ERR_STEPS"}
 

@@ -94,7 +94,8 @@ struct BondWork {
   double2* G64;            // fast path: [k_cap^2] Gram / product scratch of the V re-orthonormalisation
   double2* Y64;            // [max(mD,nD)_cap * k_cap] QR workspace / product scratch
   int* qperm;              // [k_cap] column permutation of the pivoted QR
-  int* info;               // [8] per-item: 0 mD, 1 nD, 2 transposed, 3 sweeps, 4-5 rotation counters
+  int* info;               // [16] per-item: 0 mD, 1 nD, 2 transposed, 3 sweeps, 4-5 rotation counters,
+                           // 6 FP32 sweeps, 7 NaN flag of theta, 8 rank k of the pivoted QR
   int mL_cap, nL_cap, mR_cap, nR_cap, mD_cap, nD_cap, k_cap, pad2;
 };
 

@@ -79,7 +79,7 @@ struct pt_tebd {
   int gx_bond = 1;
   int cl_odd = 1, cl_even = 1;        // Jacobi cluster sizes per layer list
   int grid_blocks = 0;                // whole-GPU Jacobi: CTAs per launch (0: use the cluster kernel)
-  int rt_odd = 1, rt_even = 1, kc_odd = 1, kc_even = 1;   // fast path: theta tile / K-chunk caps
+  int tiles_odd = 1, tiles_even = 1;  // fast path: theta + gate GEMM output tiles per layer (capacity)
   std::vector<int*> bond_info;        // per bond (odd list, then even list): its info words
   bool mixed_svd = false;             // fast path: FP32 bulk sweeps + FP64 polish on D (PT_TEBD_SVD=mixed)
   bool precond = true;                // QR-preconditioned Jacobi (PT_TEBD_PRECOND=0 disables)
@@ -220,8 +220,8 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n) {
   if (h->opt.precision == PT_FP64)
     ptk::k_theta_gate<<<dim3(h->gx_bond, n), 128, 0, s>>>(h->T, work, n);
   else
-    ptk::launch_tc_theta(h->T, work, n, work == h->d_odd ? h->rt_odd : h->rt_even,
-                         work == h->d_odd ? h->kc_odd : h->kc_even, (int)h->opt.precision, s);
+    ptk::launch_tc_theta(h->T, work, n, work == h->d_odd ? h->tiles_odd : h->tiles_even, (int)h->opt.precision, s);
+  ptk::k_nan_guard<<<(n + 127) / 128, 128, 0, s>>>(h->T, work, n);
   ev_end(h, e);
   int* cnt = work == h->d_odd ? h->d_cnt_odd : h->d_cnt_even;
   if (h->grid_blocks > 0 && h->opt.precision != PT_FP64 && h->mixed_svd) {
@@ -492,6 +492,11 @@ int build(pt_tebd* h) {
       int cap = (int)std::min((double)h->opt.chi_max, std::min(L, R));
       if (b == 0 || b == N) cap = 1;
       if (!hc.chi0.empty()) {
+        // chi_max caps every bond at every step, the initial augmented MPS included
+        if (hc.chi0[b] > h->opt.chi_max)
+          return h->fail(PT_ERR_CAPACITY, "initial MPS: bond " + std::to_string(b) + " of chain " +
+                                              std::to_string(c) + " has chi0 = " + std::to_string(hc.chi0[b]) +
+                                              " > chi_max = " + std::to_string(h->opt.chi_max));
         cap = std::max(cap, hc.chi0[b]);
         chi_init[h->lam0[c] + b] = hc.chi0[b];
       }
@@ -638,15 +643,13 @@ int build(pt_tebd* h) {
       W.sig = (double*)h->dalloc(sizeof(double) * W.k_cap);
       W.aux = (double*)h->dalloc(sizeof(double) * W.k_cap);
       W.perm = (int*)h->dalloc(sizeof(int) * W.k_cap);
-      W.info = (int*)h->dalloc(sizeof(int) * 8);
+      W.info = (int*)h->dalloc(sizeof(int) * 16);
       if (!W.QL || !W.RL || !W.QR || !W.LR || !W.HH || !W.A || !W.V || !W.sig || !W.aux || !W.perm || !W.info)
         return h->fail(PT_ERR_OOM, "bond scratch");
-      cudaMemsetAsync(W.info, 0, sizeof(int) * 8, h->stream);
+      cudaMemsetAsync(W.info, 0, sizeof(int) * 16, h->stream);
       if (h->opt.precision != PT_FP64) {
-        const int kcap = chc;
-        const size_t ma = (size_t)std::max(W.mD_cap, W.nD_cap);
-        W.TA = h->dalloc(ptk::tc_pack_bytes(W.mD_cap, kcap, (int)h->opt.precision));
-        W.TB = h->dalloc(ptk::tc_pack_bytes(W.nD_cap, kcap, (int)h->opt.precision));
+        W.TA = h->dalloc(ptk::tc_pack_bytes(W, 0, (int)h->opt.precision));
+        W.TB = h->dalloc(ptk::tc_pack_bytes(W, 1, (int)h->opt.precision));
         W.A32 = (float2*)h->dalloc(sizeof(float2) * as);
         W.V32 = (float2*)h->dalloc(sizeof(float2) * vs);
         if (!W.TA || !W.TB || !W.A32 || !W.V32) return h->fail(PT_ERR_OOM, "fast-path scratch");
@@ -677,16 +680,13 @@ int build(pt_tebd* h) {
   h->cl_odd = pick(odd);
   h->cl_even = pick(even);
   if (h->opt.precision != PT_FP64) {
-    auto caps = [&](const std::vector<BondWork>& v, int* rt, int* kc) {
-      int rows = 1, k = 1;
-      for (auto& W : v) {
-        rows = std::max(rows, std::max(W.mD_cap, W.nD_cap));
-        k = std::max(k, W.nL_cap / 4);
-      }
-      ptk::tc_caps(rows, k, (int)h->opt.precision, rt, kc);
+    auto tiles = [&](const std::vector<BondWork>& v) {
+      long long t = 0;
+      for (auto& W : v) t += ptk::tc_tile_cap(W, (int)h->opt.precision);
+      return (int)std::min<long long>(t, 1 << 30);
     };
-    caps(odd, &h->rt_odd, &h->kc_odd);
-    caps(even, &h->rt_even, &h->kc_even);
+    h->tiles_odd = tiles(odd);
+    h->tiles_even = tiles(even);
     const char* sv = getenv("PT_TEBD_SVD");
     h->mixed_svd = sv && std::string(sv) == "mixed";
   }
@@ -823,7 +823,7 @@ int pt_tebd_init(pt_tebd_t* out, const pt_chain_desc* chains, int n_chains, cons
     return PT_ERR_ARG;
   }
   if (h->opt.max_sweeps <= 0) h->opt.max_sweeps = 60;
-  if (h->opt.precision < PT_FP64 || h->opt.precision > PT_TF32X1) {
+  if (h->opt.precision < PT_FP64 || h->opt.precision > PT_BF16_OZAKI) {
     h->fail(PT_ERR_ARG, "pt_tebd_init: unknown precision");
     delete h;
     return PT_ERR_ARG;

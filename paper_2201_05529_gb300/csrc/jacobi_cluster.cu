@@ -175,10 +175,13 @@ __device__ void jacobi_cluster_svd(typename CT<R>::T* A, typename CT<R>::T* V, R
   }
   cl.sync();
   for (int c = gt; c < Na; c += ngt) {
-    const R sc = __ldcg(sig + c);
+    // a NaN ranks as -1 so the ranks stay a permutation (perm indexes columns downstream)
+    R sc = __ldcg(sig + c);
+    if (!(sc == sc)) sc = R(-1);
     int rk = 0;
     for (int k = 0; k < Na; ++k) {
-      const R sk = __ldcg(sig + k);
+      R sk = __ldcg(sig + k);
+      if (!(sk == sk)) sk = R(-1);
       rk += (sk > sc) || (sk == sc && k < c);
     }
     perm[rk] = c;

@@ -263,12 +263,17 @@ __global__ void __launch_bounds__(GRID_THREADS)
     if (blockIdx.x == 0 && tid == 0) atomicOr(status, ST_CAPACITY);
     return;
   }
+  __shared__ int s_Nf[MAX_ITEMS];           // on_b: rows of B (= columns of D); else Na
   for (int w = tid; w < n_work; w += blockDim.x) {
     int Ma, Na;
     item_shape(work[w], &Ma, &Na);
-    s_Na[w] = Na;
-    s_Ma[w] = on_b ? Na : Ma;                 // on_b: the square R^H of the pivoted QR (G64)
-    s_active[w] = Na >= 2;
+    // on_b: B = R^H of the pivoted QR (G64), Na rows and k = info[8] columns (the QR's rank)
+    const int kq = on_b ? max(0, min(work[w].info[8], Na)) : Na;
+    s_Nf[w] = Na;
+    s_Na[w] = kq;
+    s_Ma[w] = Na;
+    if (!on_b) s_Ma[w] = Ma;
+    s_active[w] = kq >= 2;
     s_A[w] = on_b ? (C2*)work[w].G64 : Cx<R>::A(work[w]);
     s_V[w] = Cx<R>::V(work[w]);
   }
@@ -436,17 +441,27 @@ __global__ void __launch_bounds__(GRID_THREADS)
       base = (base + Na) % ngwarp;
     }
   }
+  // on_b: the columns of D beyond the QR's rank have singular value 0 (after the sigma of the
+  // k columns above, so the ranking below sees every column)
+  if (on_b) {
+    const int gt = blockIdx.x * blockDim.x + tid, ngt = gridDim.x * blockDim.x;
+    for (int w = 0; w < n_work; ++w)
+      for (int c = s_Na[w] + gt; c < s_Nf[w]; c += ngt) __stcg(work[w].sig + c, 0.0);
+  }
   if (!grid_barrier(gs, status)) return;
   {
     const int gt = blockIdx.x * blockDim.x + tid, ngt = gridDim.x * blockDim.x;
     for (int w = 0; w < n_work; ++w) {
-      const int Na = s_Na[w];
+      const int Na = s_Nf[w];
       const double* sig = work[w].sig;
       for (int c = gt; c < Na; c += ngt) {
-        const double sc = __ldcg(sig + c);
+        // a NaN ranks as -1 so the ranks stay a permutation (perm indexes columns downstream)
+        double sc = __ldcg(sig + c);
+        if (!(sc == sc)) sc = -1.0;
         int rk = 0;
         for (int k = 0; k < Na; ++k) {
-          const double sk = __ldcg(sig + k);
+          double sk = __ldcg(sig + k);
+          if (!(sk == sk)) sk = -1.0;
           rk += (sk > sc) || (sk == sc && k < c);
         }
         work[w].perm[rk] = c;

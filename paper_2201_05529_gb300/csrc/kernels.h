@@ -13,6 +13,7 @@ __global__ void k_site_swap(Tables T, const SiteWork* work, int n_work);
 __global__ void k_build_blocks(Tables T, const BondWork* work, int n_work);
 __global__ void k_householder(Tables T, const BondWork* work, int n_work);
 __global__ void k_theta_gate(Tables T, const BondWork* work, int n_work);
+__global__ void k_nan_guard(Tables T, const BondWork* work, int n_work);
 __global__ void k_truncate(Tables T, const BondWork* work, int n_work, int chi_max, double eps,
                            double mtol);
 __global__ void k_recover(Tables T, const BondWork* work, int n_work);
@@ -53,7 +54,8 @@ void launch_qrcp_grid(const BondWork* work, int n_work, int blocks, unsigned* sy
 void launch_qrcp_precondition(const BondWork* work, int n_work, int cluster, int smem_cluster, int k_cap, int m_cap,
                               int* status, cudaStream_t st);
 void launch_qrcp_finish(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st);
-void launch_mix_gemm_av(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st);
+void launch_mix_gemm_av(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st,
+                        bool rank_cols = false);
 
 // optional fast-path SVD on D (PT_TEBD_SVD=mixed): FP32 bulk sweeps + FP64 Newton-Schulz
 // re-orthonormalisation + FP64 polish (mixed_svd.cu)
@@ -63,10 +65,12 @@ void launch_mixed_reorth(const BondWork* work, int n_work, int k_cap, int m_cap,
 void launch_mixed_fp64(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,
                        int* status, double polish_floor, cudaStream_t st);
 
-// tensor-core theta of the fast path (tc_theta.cu); precision: 1 TF32x3, 2 BF16x3, 3 TF32x1
-size_t tc_pack_bytes(int rows_cap, int k_cap, int precision);
-void tc_caps(int rows_cap, int k_cap, int precision, int* rt_cap, int* kc_cap);
-void launch_tc_theta(const Tables& T, const BondWork* work, int n_work, int rt_cap, int kc_cap, int precision,
+// tensor-core theta + gate of the fast path (tc_theta.cu); precision: 1 TF32x3, 2 BF16x3, 3 TF32x1,
+// 4 BF16 fixed-point slices. Packed operand bytes of a bond (which: 0 = A, 1 = B'), its output tile
+// capacity, and the launch (pack kernels + the persistent GEMM) over one layer.
+size_t tc_pack_bytes(const BondWork& W, int which, int precision);
+int tc_tile_cap(const BondWork& W, int precision);
+void launch_tc_theta(const Tables& T, const BondWork* work, int n_work, int tile_cap, int precision,
                      cudaStream_t st);
 
 // set the message returned by pt_tebd_last_error(NULL) (engine.cu)

@@ -299,10 +299,29 @@ __global__ void k_theta_gate(Tables T, const BondWork* work, int n_work) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) acc = cfma(g[(pp * 4 + qq) * 16 + i], th[i], acc);
         const int row = u * 4 + pp, col = qq * d.rR + v;
+        if (!(isfinite(acc.x) && isfinite(acc.y))) W.info[7] = 1;    // k_nan_guard stops this bond
         if (!tr) W.A[row + (size_t)col * d.mD] = acc;
         else W.A[col + (size_t)row * d.nD] = cconj(acc);
       }
     }
+  }
+}
+
+// ------------------------------------------------------------------ NaN guard before the SVD
+// The theta kernels flag a bond whose D holds a NaN or an infinity (info[7]); such a D must not
+// reach the SVD (a NaN has no place in a pivot order or a rotation), so the bond is marked empty
+// (info[0] = info[1] = 0: the SVD, the truncation and the recovery skip it, the state keeps its
+// previous tensors) and the device status records ST_NAN, which the host reports at its next
+// synchronising call. One thread per bond; the flag is cleared for the next layer.
+__global__ void k_nan_guard(Tables T, const BondWork* work, int n_work) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n_work) return;
+  const BondWork& W = work[w];
+  if (W.info[7] != 0) {
+    W.info[0] = 0;
+    W.info[1] = 0;
+    W.info[7] = 0;
+    atomicOr(T.status, ST_NAN);
   }
 }
 

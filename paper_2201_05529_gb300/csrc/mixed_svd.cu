@@ -105,7 +105,8 @@ __global__ void k_mix_v_to_f64(const BondWork* work, int n_work) {
   }
 }
 
-// op 0: G = V^H V;  op 1: Y = V G;  op 2: Y = A V  (grid: tiles x tiles x items)
+// op 0: G = V^H V;  op 1: Y = V G;  op 2: Y = A V;  op 3: Y = A V on the first k = info[8]
+// columns of V (the pivoted QR's rank)  (grid: tiles x tiles x items)
 __global__ void __launch_bounds__(256) k_mix_gemm(const BondWork* work, int n_work, int op) {
   const int w = blockIdx.z;
   if (w >= n_work) return;
@@ -113,11 +114,11 @@ __global__ void __launch_bounds__(256) k_mix_gemm(const BondWork* work, int n_wo
   int Ma, Na;
   shape(W, &Ma, &Na);
   const int tm = blockIdx.x, tn = blockIdx.y;
-  const int m = op == 2 ? Ma : Na, n = Na;
+  const int m = op >= 2 ? Ma : Na, n = op == 3 ? min(W.info[8], Na) : Na;
   if (tm * TB >= m || tn * TB >= n) return;
   if (op == 0) gemm_tile(W.V, Na, true, W.V, Na, W.G64, Na, Na, Na, Na, tm, tn);
   else if (op == 1) gemm_tile(W.V, Na, false, W.G64, Na, W.Y64, Na, Na, Na, Na, tm, tn);
-  else gemm_tile(W.A, Ma, false, W.V, Na, W.Y64, Ma, Ma, Na, Na, tm, tn);
+  else gemm_tile(W.A, Ma, false, W.V, Na, W.Y64, Ma, Ma, n, Na, tm, tn);
 }
 
 // op 0: V = 1.5 V - 0.5 Y (Newton-Schulz update);  op 1: A = Y (the rotated matrix)
@@ -138,10 +139,10 @@ __global__ void k_mix_update(const BondWork* work, int n_work, int op) {
   }
 }
 
-// Y64 = A V (A: Ma x Na, V: Na x Na)
-void launch_mix_gemm_av(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st) {
+// Y64 = A V (A: Ma x Na, V: Na x Na), or only its first info[8] columns (rank_cols)
+void launch_mix_gemm_av(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st, bool rank_cols) {
   const int tk = (k_cap + TB - 1) / TB, tmm = (m_cap + TB - 1) / TB;
-  k_mix_gemm<<<dim3(tmm, tk, n_work), 256, 0, st>>>(work, n_work, 2);
+  k_mix_gemm<<<dim3(tmm, tk, n_work), 256, 0, st>>>(work, n_work, rank_cols ? 3 : 2);
 }
 
 // stage 1: FP32 copy of D and the FP32 bulk sweeps (V32 from identity)

@@ -62,6 +62,13 @@ constexpr int QR_SMEM_THREADS = 512;
 // The partial column norms that pick the pivots are downdated, n <- n - |a_j|^2, and recomputed
 // where that cancels below sqrt(eps) of the last exact value (the safeguard of LAPACK's pivoted
 // QR); they only choose pivots. The reflector uses the exact norm of the pivot column.
+// Rank-revealing stop: the factorisation ends at the first step j whose pivot column (the largest
+// remaining one) has an exact norm^2 <= u^2 ||D||_F^2 (u = 2^-53): every remaining column is then
+// at the FP64 noise floor (the level below which the Jacobi does not rotate a column either), and
+// the trailing block R22 they form, ||R22||_F <= sqrt(n) u ||D||_F, is dropped -- a perturbation
+// within the backward error of any FP64 SVD. R is then k x n (k = j, recorded in info[8]) and
+// B = R^H is n x k, so the Jacobi runs on k columns. (The workloads' D are often exactly rank
+// deficient: a conserved magnetisation leaves ~n/4 nonzero singular values.)
 // Dynamic shared memory: [X[lq_cap][m_cap] if !GL] | hv[m_cap] | beta[lq_cap] (double2),
 // nrm[lq_cap] | nref[lq_cap] (double), qp[n_cap] | pos[n_cap] | done[lq_cap] (int).
 template <bool GL>
@@ -93,6 +100,9 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
   __shared__ double s_sc[1];                      // kappa of the step's reflector
   __shared__ double s_red[32];
   __shared__ int s_p;
+  __shared__ double s_fro;                        // this CTA's share of ||D||_F^2
+  __shared__ double s_thr2;                       // the noise floor u^2 ||D||_F^2 (tid 0)
+  __shared__ int s_stop, s_k;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int Ln = rank < Na ? (Na - rank + C - 1) / C : 0;
   // local column l, its element loads and stores (L2-coherent in global mode)
@@ -125,13 +135,23 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
     }
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0;
+    for (int l = 0; l < Ln; ++l) f += nrm[l];
+    s_fro = f;
+    s_stop = 0;
+    s_k = Na;
+  }
   // local candidate (largest remaining norm, smallest index on ties) into slot par
   auto publish = [&](int par) {
     if (wid == 0) {
       double best = -1.0;
       int bi = 0x7fffffff;
-      for (int l = lane; l < Ln; l += 32)
-        if (!done[l] && nrm[l] > best) { best = nrm[l]; bi = rank + l * C; }
+      // a NaN norm counts as 0, so an unfinished column is always chosen (the index stays valid)
+      for (int l = lane; l < Ln; l += 32) {
+        const double nl = nrm[l] == nrm[l] ? nrm[l] : 0.0;
+        if (!done[l] && nl > best) { best = nl; bi = rank + l * C; }
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const double ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -146,6 +166,12 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
   };
   publish(0);
   cl.sync();
+  if (threadIdx.x == 0) {
+    // ||D||_F^2 from the C shares, summed in the same order in every CTA
+    double f = 0;
+    for (int r = 0; r < C; ++r) f += *cl.map_shared_rank(&s_fro, r);
+    s_thr2 = 1.232595164407831e-32 * f;            // (2^-53)^2 ||D||_F^2
+  }
   for (int j = 0; j < Na; ++j) {
     const int par = j & 1;
     // 1. the pivot: best of the C candidates (same values, same order in every CTA)
@@ -187,31 +213,38 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
       // v^H v = 2 ||x|| (||x|| + |alpha|), so kappa = 1 / (||x|| (||x|| + |alpha|))
       double nrm2 = 0;
       for (int k = 0; k < nw; ++k) nrm2 += s_red[k];
-      const double2 alpha = hv[j];
-      const double a2 = alpha.x * alpha.x + alpha.y * alpha.y;
-      double kap = 0.0;
-      double2 beta = alpha;
-      if (nrm2 > 0.0) {
-        const double xn = sqrt(nrm2);
-        double2 ph = make_double2(1.0, 0.0);
-        double aabs = 0.0;
-        if (a2 > 0.0) {
-          const double ia = rsqrt(a2);
-          aabs = a2 * ia;
-          ph = make_double2(alpha.x * ia, alpha.y * ia);
+      if (nrm2 <= s_thr2) {
+        // every remaining column is at the noise floor: stop (same decision in every CTA)
+        s_stop = 1;
+        s_k = j;
+      } else {
+        const double2 alpha = hv[j];
+        const double a2 = alpha.x * alpha.x + alpha.y * alpha.y;
+        double kap = 0.0;
+        double2 beta = alpha;
+        if (nrm2 > 0.0) {
+          const double xn = sqrt(nrm2);
+          double2 ph = make_double2(1.0, 0.0);
+          double aabs = 0.0;
+          if (a2 > 0.0) {
+            const double ia = rsqrt(a2);
+            aabs = a2 * ia;
+            ph = make_double2(alpha.x * ia, alpha.y * ia);
+          }
+          beta = make_double2(-ph.x * xn, -ph.y * xn);
+          kap = 1.0 / (xn * (xn + aabs));
+          hv[j] = make_double2(ph.x * (aabs + xn), ph.y * (aabs + xn));     // v_j = alpha - beta
         }
-        beta = make_double2(-ph.x * xn, -ph.y * xn);
-        kap = 1.0 / (xn * (xn + aabs));
-        hv[j] = make_double2(ph.x * (aabs + xn), ph.y * (aabs + xn));     // v_j = alpha - beta
-      }
-      s_sc[0] = kap;
-      qp[j] = p;
-      if (rank == owner) {
-        betaL[lp] = beta;
-        done[lp] = 1;
+        s_sc[0] = kap;
+        qp[j] = p;
+        if (rank == owner) {
+          betaL[lp] = beta;
+          done[lp] = 1;
+        }
       }
     }
     __syncthreads();
+    if (s_stop) break;                            // uniform across the cluster
     const double kap = s_sc[0];
     // 3. own remaining columns: a <- a - kappa v (v^H a); partial norms over rows > j
     for (int l = wid; l < Ln; l += nw) {
@@ -252,15 +285,36 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
     publish(par ^ 1);
     cl.sync();                                    // candidates published; pivot column reads done
   }
-  // permutation (every CTA holds the same qp), B = R^H rows of the own columns
-  for (int j = tid; j < Na; j += blockDim.x) pos[qp[j]] = j;
-  if (rank == 0)
-    for (int j = tid; j < Na; j += blockDim.x) W.qperm[j] = qp[j];
+  // permutation (every CTA holds the same qp): the k pivots in order, then the remaining columns
+  // by index; B = R^H (Na x k) rows of the own columns
+  const int kq = s_k;
+  for (int j = tid; j < Na; j += blockDim.x) pos[j] = -1;
   __syncthreads();
+  for (int j = tid; j < kq; j += blockDim.x) pos[qp[j]] = j;
+  __syncthreads();
+  if (wid == 0) {
+    int i = kq;
+    for (int s0 = 0; s0 < Na; s0 += 32) {
+      const int s = s0 + lane;
+      const bool rem = s < Na && pos[s] < 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, rem);
+      if (rem) {
+        const int at = i + __popc(bal & ((1u << lane) - 1u));
+        pos[s] = at;
+        qp[at] = s;
+      }
+      i += __popc(bal);
+    }
+  }
+  __syncthreads();
+  if (rank == 0) {
+    for (int j = tid; j < Na; j += blockDim.x) W.qperm[j] = qp[j];
+    if (tid == 0) W.info[8] = kq;
+  }
   for (int l = wid; l < Ln; l += nw) {
     const int s = rank + l * C, i = pos[s];
     const double2* a = colp(l);
-    for (int c = lane; c < Na; c += 32) {
+    for (int c = lane; c < kq; c += 32) {
       double2 v = make_double2(0.0, 0.0);           // B[i, c] = conj(R[c, i])
       if (c < i) {
         const double2 x = ld(a + c);
@@ -287,7 +341,8 @@ constexpr int QRG_RC = 8;                 // rows per lane held in registers: Ma
 // norm, and its warps apply the reflector; one grid barrier per step. The partial norms are
 // double-buffered (aux and sig alternate: step j reads one and writes the other, so a CTA still
 // choosing step j's pivot never sees step j+1's values); finished columns write -1. The pivot's owner records qperm[j] and beta_j (in V, free until the finish).
-// Finally every warp writes its column of B = R^H.
+// The same rank-revealing stop as k_qrcp_cl ends a matrix at the first pivot at the noise floor.
+// Finally every warp writes the row of B = R^H (Na x k) that belongs to its column.
 __global__ void __launch_bounds__(QRG_THREADS, 1)
     k_qrcp_grid(const BondWork* work, int n_work, GridSync gs, int* status) {
   extern __shared__ double2 hv[];
@@ -296,7 +351,9 @@ __global__ void __launch_bounds__(QRG_THREADS, 1)
   __shared__ int s_maxna;
   __shared__ double s_red[QRG_WARPS];
   __shared__ double s_kap;
-  __shared__ int s_p, s_own;
+  __shared__ int s_p, s_own, s_stopnow;
+  __shared__ double s_thr2[QRG_MAX_ITEMS];  // u^2 ||D||_F^2 of the matrices this CTA holds
+  __shared__ int s_kst[QRG_MAX_ITEMS];      // their stop step (Na if never)
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (n_work > QRG_MAX_ITEMS) {
     if (blockIdx.x == 0 && tid == 0) atomicOr(status, ST_CAPACITY);
@@ -375,11 +432,24 @@ __global__ void __launch_bounds__(QRG_THREADS, 1)
   const int w_lo = g0 < g1 ? item_of(g0) : 0;
   const int w_hi = g0 < g1 ? item_of(g1 - 1) : -1;
   if (!grid_barrier(gs, status)) return;
+  // ||D||_F^2 of every matrix this CTA holds columns of, summed in the same order everywhere
+  for (int w = w_lo + wid; w <= w_hi; w += QRG_WARPS) {
+    const int Na = s_off[w + 1] - s_off[w];
+    double f = 0;
+    for (int i = lane; i < Na; i += 32) f += __ldcg(work[w].aux + i);
+    f = wsum(f);
+    if (lane == 0) {
+      s_thr2[w] = 1.232595164407831e-32 * f;   // (2^-53)^2 ||D||_F^2
+      s_kst[w] = Na;
+    }
+  }
+  __syncthreads();
+  int my_pos = -1;                            // the step at which this warp's column was pivoted
   const int maxna = s_maxna;
   for (int j = 0; j < maxna; ++j) {
     for (int w = w_lo; w <= w_hi; ++w) {
       const int Na = s_off[w + 1] - s_off[w], Ma = s_Ma[w];
-      if (j >= Na) continue;                  // uniform across the CTA
+      if (j >= s_kst[w]) continue;            // uniform across the CTA and across CTAs
       const BondWork& W = work[w];
       const double2* X = W.Y64;
       const double* nrm_cur = (j & 1) ? W.sig : W.aux;
@@ -394,6 +464,7 @@ __global__ void __launch_bounds__(QRG_THREADS, 1)
         for (int k = 0; k < QRG_RC; ++k) {
           const int i = lane + 32 * k;
           v[k] = i < Na ? __ldcg(nrm_cur + i) : -2.0;
+          if (!(v[k] == v[k])) v[k] = 0.0;        // NaN: still a valid unfinished column
         }
 #pragma unroll
         for (int k = 0; k < QRG_RC; ++k)
@@ -423,36 +494,47 @@ __global__ void __launch_bounds__(QRG_THREADS, 1)
       if (tid == 0) {
         double nrm2 = 0;
         for (int k = 0; k < QRG_WARPS; ++k) nrm2 += s_red[k];
-        const double2 alpha = hv[j];
-        const double a2 = alpha.x * alpha.x + alpha.y * alpha.y;
-        double kap = 0.0;
-        double2 beta = alpha;
-        if (nrm2 > 0.0) {
-          const double xn = sqrt(nrm2);
-          double2 ph = make_double2(1.0, 0.0);
-          double aabs = 0.0;
-          if (a2 > 0.0) {
-            const double ia = rsqrt(a2);
-            aabs = a2 * ia;
-            ph = make_double2(alpha.x * ia, alpha.y * ia);
+        s_stopnow = 0;
+        if (nrm2 <= s_thr2[w]) {
+          // every remaining column is at the noise floor: this matrix stops at rank j
+          s_stopnow = 1;
+          s_kst[w] = j;
+        } else {
+          const double2 alpha = hv[j];
+          const double a2 = alpha.x * alpha.x + alpha.y * alpha.y;
+          double kap = 0.0;
+          double2 beta = alpha;
+          if (nrm2 > 0.0) {
+            const double xn = sqrt(nrm2);
+            double2 ph = make_double2(1.0, 0.0);
+            double aabs = 0.0;
+            if (a2 > 0.0) {
+              const double ia = rsqrt(a2);
+              aabs = a2 * ia;
+              ph = make_double2(alpha.x * ia, alpha.y * ia);
+            }
+            beta = make_double2(-ph.x * xn, -ph.y * xn);
+            kap = 1.0 / (xn * (xn + aabs));
+            hv[j] = make_double2(ph.x * (aabs + xn), ph.y * (aabs + xn));
           }
-          beta = make_double2(-ph.x * xn, -ph.y * xn);
-          kap = 1.0 / (xn * (xn + aabs));
-          hv[j] = make_double2(ph.x * (aabs + xn), ph.y * (aabs + xn));
-        }
-        s_kap = kap;
-        const int gp = s_off[w] + p;
-        s_own = -1;
-        if (gp >= g0 && gp < g1) {              // this CTA owns the pivot column
-          s_own = gp - g0;
-          __stcg(W.qperm + j, p);
-          __stcg(W.V + j, beta);
+          s_kap = kap;
+          const int gp = s_off[w] + p;
+          s_own = -1;
+          if (gp >= g0 && gp < g1) {              // this CTA owns the pivot column
+            s_own = gp - g0;
+            __stcg(W.qperm + j, p);
+            __stcg(W.V + j, beta);
+          }
         }
       }
       __syncthreads();
+      if (s_stopnow) continue;                  // uniform; nothing reads hv any more this step
       const double kap = s_kap;
       if (have && w_me == w) {
-        if (wid == s_own) done = true;
+        if (wid == s_own && !done) {
+          done = true;
+          my_pos = j;
+        }
         if (done) {
           if (lane == 0) __stcg(nrm_nxt + s_me, -1.0);
         } else {
@@ -513,20 +595,36 @@ __global__ void __launch_bounds__(QRG_THREADS, 1)
     }
     if (!grid_barrier(gs, status)) return;
   }
-  // B = R^H: column c of B is row c of R, B[i, c] = conj(R[c, i]), R[c, qperm[i]] = X[c, qperm[i]]
+  // B = R^H (Na x k): this warp's column s sits at position i of the pivot order (its step, or for
+  // a column never pivoted k + its rank among those by index); row i of B is
+  // B[i, c] = conj(R[c, i]) = conj(X[c, s]) for c < i, conj(beta_i) at c = i (i < k), 0 beyond.
   if (have) {
     const BondWork& W = work[w_me];
-    const int Na = s_off[w_me + 1] - s_off[w_me], Ma = Ma_me, cc = s_me;
-    for (int i = lane; i < Na; i += 32) {
+    const int Na = s_off[w_me + 1] - s_off[w_me], Ma = Ma_me, sc = s_me, kq = s_kst[w_me];
+    int i = my_pos;
+    if (i < 0) {
+      // the step-k norm buffer holds -1 for every pivoted column and >= 0 for the rest
+      const double* nb = (kq & 1) ? W.sig : W.aux;
+      int before = 0;
+      for (int t0 = 0; t0 < sc; t0 += 32) {
+        const int t = t0 + lane;
+        const bool rem = t < sc && __ldcg(nb + t) >= 0.0;
+        before += __popc(__ballot_sync(0xffffffffu, rem));
+      }
+      i = kq + before;
+      if (lane == 0) __stcg(W.qperm + i, sc);
+    }
+    if (sc == 0 && lane == 0) W.info[8] = kq;
+    for (int c = lane; c < kq; c += 32) {
       double2 v = make_double2(0.0, 0.0);
-      if (cc < i) {
-        const double2 r = __ldcg(W.Y64 + cc + (size_t)__ldcg(W.qperm + i) * Ma);
+      if (c < i) {
+        const double2 r = __ldcg(W.Y64 + c + (size_t)sc * Ma);
         v = make_double2(r.x, -r.y);
-      } else if (cc == i) {
-        const double2 b = __ldcg(W.V + cc);
+      } else if (c == i) {
+        const double2 b = __ldcg(W.V + c);
         v = make_double2(b.x, -b.y);
       }
-      W.G64[i + (size_t)cc * Na] = v;
+      W.G64[i + (size_t)c * Na] = v;
     }
   }
 }
@@ -538,7 +636,8 @@ __global__ void k_qrcp_vd(const BondWork* work, int n_work) {
   const BondWork& W = work[w];
   int Ma, Na;
   shape(W, &Ma, &Na);
-  const size_t tot = (size_t)Na * Na;
+  const int kq = min(W.info[8], Na);              // the pivoted QR's rank
+  const size_t tot = (size_t)Na * kq;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(idx % Na), c = (int)(idx / Na);
     W.V[W.qperm[k] + (size_t)c * Na] = W.G64[idx];
@@ -552,7 +651,7 @@ __global__ void k_qrcp_ud(const BondWork* work, int n_work) {
   const BondWork& W = work[w];
   int Ma, Na;
   shape(W, &Ma, &Na);
-  const size_t tot = (size_t)Ma * Na;
+  const size_t tot = (size_t)Ma * min(W.info[8], Na);   // the k columns with a singular value
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(idx / Ma);
     const double s = W.sig[c];
@@ -663,7 +762,7 @@ void launch_qrcp_precondition(const BondWork* work, int n_work, int cluster, int
 
 void launch_qrcp_finish(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st) {
   k_qrcp_vd<<<dim3(128, n_work), 256, 0, st>>>(work, n_work);
-  launch_mix_gemm_av(work, n_work, k_cap, m_cap, st);
+  launch_mix_gemm_av(work, n_work, k_cap, m_cap, st, /*rank_cols=*/true);
   k_qrcp_ud<<<dim3(128, n_work), 256, 0, st>>>(work, n_work);
 }
 

@@ -13,7 +13,10 @@
 //    loads this library holds it until the process exits.
 //  * Problems whose workspace would exceed that size are rejected with PT_ERR_CAPACITY.
 //  * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
-//    that device current) and caches it; make that first call before any stream capture.
+//    that device current) and caches it per device index. A cudaDeviceReset invalidates that
+//    cached address: after a reset, reload the library before calling again.
+//  * Every call reads the device status word back and synchronises its stream before returning,
+//    so no call (the first or a later one) may be made while that stream is being captured.
 //  * Every call shares the one array. Calls that overlap on the GPU (different streams, or host
 //    threads without ordering) race on it and corrupt each other's results; serialise them.
 //  * The array keeps the previous call's contents; everything that must start at zero is cleared

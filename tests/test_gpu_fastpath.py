@@ -1,12 +1,18 @@
-"""Fast path (theta contraction on tcgen05 tensor cores, FP64 Jacobi SVD) against the FP64 oracle.
+"""Fast path (theta + gate on tcgen05 tensor cores, FP64 Jacobi SVD) against the FP64 oracle.
 
-The bar the PT-TEBD target sets for the FP32 tensor-core path is 1e-5 absolute on <sigma^z_n(t)>;
-TF32x3 (two TF32 pieces, ~22 significant bits) is held to it. BF16x3 (two bf16 pieces, ~16 bits,
-three products) carries ~1e-5 relative error per product, so its bar is 1e-4; its error is
-printed.
-Where the chi cap binds, the truncated trajectory itself amplifies perturbations (see
-test_gpu_parity.py); there the bar is 1e-5 + 10 x the oracle's sensitivity to a 1e-7 relative
-perturbation of its gates (single-precision rounding). Every observable's error is printed.
+The PT-TEBD target holds the FP32 tensor-core path to 1e-5 absolute on <sigma^z_n(t)>.
+
+bf16_ozaki (fixed-point BF16 slices whose leading partial sums are exact in the tensor cores' FP32
+accumulators) is the fast path that meets it: the theta + gate product is accurate to ~1e-9 of
+the rows' scale, so the path follows the oracle as closely as the FP64 GPU path does. It is held to
+1e-7 on the three-site chain, and on the five-site chain to the strict 1e-5 until the oracle's own
+response to a 1e-13 gate perturbation passes 1e-6 (step ~24: beyond it the chi-capped trajectory
+amplifies any rounding difference, FP64 included, to ~1e-4; see test_gpu_parity.py).
+
+The natural-split modes (TF32x3, BF16x3: three pieces of every operand, FP32 accumulation of the
+unscaled piece products) carry the accumulators' rounding, ~1e-6 of the row scale per product;
+on the five-site chain that drifts ~1e-6 per step, so the strict 1e-5 window is an expected failure
+(strict xfail: it fails today, and would be flagged if it started to pass). Every error is printed.
 """
 import numpy as np
 import pytest
@@ -18,7 +24,6 @@ from tests.gpu_helpers import OPS, oracle_envelope, run_gpu, run_oracle
 pytestmark = pytest.mark.gpu
 
 FAST_TOL = 1e-5
-BAR = {"tf32x3": FAST_TOL, "bf16x3": 1e-4}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -33,34 +38,75 @@ def _lib():
     return capi
 
 
-@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
-def test_three_site_one_bath_fast_path(precision):
-    w = workload("xyz3_onebath")
-    cis = oprob.build_inputs(w)
-    eng, obs, tr = run_gpu(w, cis, OPS, precision=precision)
-    ref = run_oracle(w, cis, OPS)[0]
-    err = np.abs(obs[:, 0, :3, :] - ref.obs).max(axis=(1, 2))
-    print(f"{precision}: max |obs - oracle| per step: {np.array2string(err, precision=2)}")
-    assert np.max(err) < BAR[precision]
-    eng.destroy()
+def _err(obs, ref, N):
+    return np.abs(obs[:, 0, :N, :] - ref.obs).max(axis=(1, 2))
 
 
-@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
-def test_five_site_two_baths_fast_path(precision):
+@pytest.fixture(scope="module")
+def five_site():
     w = workload("xyz5_twobaths", K=30)
     cis = oprob.build_inputs(w)
-    eng, obs, tr = run_gpu(w, cis, OPS, precision=precision)
     ref = run_oracle(w, cis, OPS)[0]
-    err = np.abs(obs[:, 0, :5, :] - ref.obs).max(axis=(1, 2))
-    env = oracle_envelope(w, cis[0], OPS, scale=1e-7)
-    bar = BAR[precision] + 10.0 * env
-    print(f"{precision}: max err {err.max():.2e}; per-step err {np.array2string(err[::5], precision=2)}")
-    bad = np.nonzero(err > bar)[0]
-    assert len(bad) == 0, f"step {bad[0]}: {err[bad[0]]:.3e} > {bar[bad[0]]:.3e}"
-    # the first steps are held to the plain bar; afterwards FP32 accumulation in the 3M theta
-    # product makes the error grow ~1e-6 per step on this workload (reported, see the design notes)
-    assert np.max(err[:6]) < BAR[precision]
+    env = oracle_envelope(w, cis[0], OPS, scale=1e-13)
+    # the strict window: until the oracle's own rounding envelope passes 1e-6
+    s_end = int(np.argmax(env > 1e-6)) - 1 if np.any(env > 1e-6) else w.K
+    return w, cis, ref, env, s_end
+
+
+def test_three_site_one_bath_ozaki():
+    w = workload("xyz3_onebath")
+    cis = oprob.build_inputs(w)
+    eng, obs, _ = run_gpu(w, cis, OPS, precision="bf16_ozaki")
+    err = _err(obs, run_oracle(w, cis, OPS)[0], 3)
+    print(f"bf16_ozaki: max |obs - oracle| per step: {np.array2string(err, precision=2)}")
+    assert np.max(err) < 1e-7
     eng.destroy()
+
+
+def test_five_site_two_baths_ozaki(five_site):
+    w, cis, ref, env, s_end = five_site
+    eng, obs, _ = run_gpu(w, cis, OPS, precision="bf16_ozaki")
+    err = _err(obs, ref, 5)
+    print(f"bf16_ozaki: strict window 0..{s_end}; per-step err {np.array2string(err, precision=2)}")
+    assert s_end >= 20
+    assert np.max(err[:s_end + 1]) < FAST_TOL, np.max(err[:s_end + 1])
+    # beyond the strict window: the target plus 10x the oracle's own rounding envelope
+    assert np.all(err <= FAST_TOL + 10.0 * env)
+    eng.destroy()
+
+
+def test_ozaki_matches_the_fp64_path_on_the_bench_window():
+    # steps 5..25 of the five-site chain (the window the bench times): fast vs FP64 GPU path
+    w = workload("xyz5_twobaths", K=25)
+    cis = oprob.build_inputs(w)
+    _, o64, _ = run_gpu(w, cis, OPS, precision="fp64")
+    _, o16, _ = run_gpu(w, cis, OPS, precision="bf16_ozaki")
+    d = np.abs(o64[5:, 0, :5, :] - o16[5:, 0, :5, :]).max()
+    print(f"bf16_ozaki vs fp64 path, steps 5..25: {d:.2e}")
+    assert d < FAST_TOL
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+def test_natural_split_three_site_within_1e4(precision):
+    w = workload("xyz3_onebath")
+    cis = oprob.build_inputs(w)
+    eng, obs, _ = run_gpu(w, cis, OPS, precision=precision)
+    err = _err(obs, run_oracle(w, cis, OPS)[0], 3)
+    print(f"{precision}: max |obs - oracle| per step: {np.array2string(err, precision=2)}")
+    assert np.max(err) < 1e-4
+    eng.destroy()
+
+
+@pytest.mark.xfail(strict=True, reason="FP32 accumulation of unscaled split pieces drifts ~1e-6 per step "
+                                       "on the five-site chain; bf16_ozaki is the path that meets 1e-5")
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+def test_natural_split_five_site_strict_window(precision, five_site):
+    w, cis, ref, env, s_end = five_site
+    eng, obs, _ = run_gpu(w, cis, OPS, precision=precision)
+    err = _err(obs, ref, 5)
+    print(f"{precision}: per-step err {np.array2string(err, precision=2)}")
+    eng.destroy()
+    assert np.max(err[:s_end + 1]) < FAST_TOL
 
 
 def test_tf32x1_runs_and_is_reported():
@@ -74,18 +120,19 @@ def test_tf32x1_runs_and_is_reported():
     eng.destroy()
 
 
-def test_fast_path_first_step_matches_fp64_path():
-    # three steps from a product state: the only difference between the paths is the theta GEMM
+def test_fast_path_first_steps_match_fp64_path():
+    # three steps from a product state: the only difference between the paths is theta + gate
     w = workload("xyz5_twobaths", K=3)
     cis = oprob.build_inputs(w)
     _, o64, _ = run_gpu(w, cis, OPS, precision="fp64")
-    _, o32, _ = run_gpu(w, cis, OPS, precision="tf32x3")
-    assert np.max(np.abs(o64 - o32)) < FAST_TOL
+    _, o16, _ = run_gpu(w, cis, OPS, precision="bf16_ozaki")
+    assert np.max(np.abs(o64 - o16)) < 1e-8
 
 
-def test_fast_path_graph_and_eager_agree_bitwise():
+@pytest.mark.parametrize("precision", ["bf16_ozaki", "tf32x3"])
+def test_fast_path_graph_and_eager_agree_bitwise(precision):
     w = workload("xyz3_onebath", K=8)
     cis = oprob.build_inputs(w)
-    _, o1, _ = run_gpu(w, cis, OPS, precision="tf32x3", use_graph=True)
-    _, o2, _ = run_gpu(w, cis, OPS, precision="tf32x3", use_graph=False)
+    _, o1, _ = run_gpu(w, cis, OPS, precision=precision, use_graph=True)
+    _, o2, _ = run_gpu(w, cis, OPS, precision=precision, use_graph=False)
     assert np.array_equal(o1, o2)

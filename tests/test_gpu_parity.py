@@ -32,10 +32,21 @@ def _lib():
     return capi
 
 
+def _state_matches(eng, c, N, chis, kappas, lams, lognorm, tol):
+    chi, kap = eng.get_dims(c)
+    assert list(chi) == list(chis), (list(chi), chis)
+    assert list(kap) == list(kappas)
+    for b in range(1, N):
+        lam = eng.get_lambda(c, b)
+        assert np.max(np.abs(lam - lams[b])) < tol
+    assert abs(eng.get_lognorm(c) - lognorm) < tol
+
+
 def _compare(w, cis, K=None, insert=None, tol=TOL, chis=True, envelope=False):
     K = w.K if K is None else K
     eng, obs, tr = run_gpu(w, cis, OPS, K=K, insert=insert)
     ref = run_oracle(w, cis, OPS, K=K, insert=insert)
+    strict_windows = []
     for c, r in enumerate(ref):
         N = cis[c].N
         err = np.abs(obs[:, c, :N, :] - r.obs).max(axis=(1, 2))
@@ -44,20 +55,28 @@ def _compare(w, cis, K=None, insert=None, tol=TOL, chis=True, envelope=False):
             bar = tol + 10.0 * oracle_envelope(w, cis[c], OPS, K=K, insert=ins)
             bad = np.nonzero(err > bar)[0]
             assert len(bad) == 0, f"chain {c}: step {bad[0]}: |obs - oracle| = {err[bad[0]]:.3e} > {bar[bad[0]]:.3e}"
-            strict = np.nonzero(bar <= 2 * tol)[0]
-            assert len(strict) > 0 and np.max(err[strict]) < tol
+            # the strict window: every step before the oracle's own envelope passes the bar
+            s_end = int(np.argmax(bar > 2 * tol)) - 1 if np.any(bar > 2 * tol) else K
+            assert s_end >= 1
+            assert np.max(err[:s_end + 1]) < tol, f"chain {c}: strict window 0..{s_end}: {np.max(err[:s_end + 1]):.3e}"
+            assert np.max(np.abs(tr[:s_end + 1, c] - r.trace[:s_end + 1])) < tol
+            strict_windows.append((c, s_end))
             continue
         assert np.max(err) < tol, f"chain {c}: max |obs - oracle| = {np.max(err):.3e}"
         assert np.max(np.abs(tr[:, c] - r.trace)) < tol
         if chis:
-            chi, kap = eng.get_dims(c)
-            assert list(chi) == list(r.chis[-1]), (list(chi), r.chis[-1])
-            assert list(kap) == list(r.kappas[-1])
-            for b in range(1, N):
-                lam = eng.get_lambda(c, b)
-                assert np.max(np.abs(lam - r.final_mps.lam[b])) < tol
-            assert abs(eng.get_lognorm(c) - r.lognorm[-1]) < tol
+            _state_matches(eng, c, N, r.chis[-1], r.kappas[-1], r.final_mps.lam, r.lognorm[-1], tol)
     eng.destroy()
+    # envelope runs: bond dims, lambdas and log-norm at the end of each strict window, from a run
+    # stopped there (the oracle keeps every step's state)
+    for c, s_end in strict_windows:
+        if s_end >= K:
+            s_end = K
+        e2, _, _ = run_gpu(w, cis, OPS, K=s_end, insert=insert)
+        r = ref[c]
+        _state_matches(e2, c, cis[c].N, r.chis[s_end], r.kappas[s_end], r.lambdas[s_end - 1],
+                       r.lognorm[s_end], tol)
+        e2.destroy()
     return obs, ref
 
 
@@ -73,9 +92,11 @@ def test_markovian_four_sites_odd_and_even_layers():
     _compare(w, oprob.build_inputs(w))
 
 
-def test_five_site_two_baths_short():
-    # chi reaches the cap 64 near step 12: strict 1e-9 before, the oracle's envelope after
-    w = workload("xyz5_twobaths", K=30)
+def test_five_site_two_baths_forty_steps():
+    # chi reaches the cap 64 near step 10; strict 1e-9 on observables and trace until the oracle's
+    # own response to a 1e-13 gate perturbation passes 2e-9 (step ~17), then the envelope; bond
+    # dims, lambdas and log-norm checked at the end of the strict window
+    w = workload("xyz5_twobaths", K=40)
     _compare(w, oprob.build_inputs(w), envelope=True)
 
 
@@ -196,12 +217,11 @@ def test_alternative_svd_routes(env, monkeypatch):
     w = workload("xyz5_twobaths", K=12, chi_max=256)
     cis = oprob.build_inputs(w)
     if "PT_TEBD_SVD" in env:
-        # a fast-path route (TF32x3 theta): the fast path's bar, 1e-5 strict over the first 6
-        # steps and 1e-5 + 10 x the oracle's response to 1e-7 perturbations afterwards
-        _, obs, _ = run_gpu(w, cis, OPS, precision="tf32x3")
+        # a fast-path route (bf16_ozaki theta + gate): the fast path's strict 1e-5 on this
+        # uncapped window
+        _, obs, _ = run_gpu(w, cis, OPS, precision="bf16_ozaki")
         ref = run_oracle(w, cis, OPS)[0]
         err = np.abs(obs[:, 0, :5, :] - ref.obs).max(axis=(1, 2))
-        bar = 1e-5 + 10.0 * oracle_envelope(w, cis[0], OPS, scale=1e-7)
-        assert np.max(err[:7]) < 1e-5 and np.all(err <= bar), (err, bar)
+        assert np.max(err) < 1e-5, err
     else:
         _compare(w, cis)
