@@ -1,19 +1,23 @@
 #!/usr/bin/env python3
 """Benchmark of the PT-TEBD time step on GB300 (site-steps/s), one JSON line on stdout.
 
-Workload (default): the five-site XYZ chain between a hot (T=5) and a cold (T=0.5) Ohmic bath,
-alpha=0.16, w_c=4, dt=0.05, PT-MPO bond <= 32, chi <= 64, eps = 1e-8 (200-step trajectory).
-A "step" is one full PT-TEBD time step of every chain (three bond layers, the PT site layer,
-three bond layers, readout). W warm-up steps run from t = 0, then K steps are timed, each with
-CUDA events on the library's stream and an L2 flush (a 256 MiB write) between timed steps.
+Workload (default): the 21-site isotropic XY chain with an Ohmic bath on every site (alpha=0.05,
+w_c=3, T=0.8), one central excitation, dt=0.1, PT-MPO bond <= 16, chi <= 128, eps = 1e-6 (a
+100-step trajectory; the largest single-GPU workload). A "step" is one full PT-TEBD time step (three
+bond layers, the PT site layer, three bond layers, readout). W warm-up steps run from t = 0, then K
+steps are timed, each with CUDA events on the library's stream and an L2 flush (a 256 MiB write)
+between timed steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32x3|fp64|bf16x3|tf32x1]
-The default times the FP32 tensor-core path (TF32x3) and, on the same window, the FP64 path.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16_ozaki|fp64|tf32x3|bf16x3|tf32x1]
+The default times the fast path (theta + gate on tensor cores from exact-accumulation BF16 slices,
+FP64 SVD) and, on the same window, the FP64 path; the five-site two-bath chain is reported as a
+secondary workload.
   python bench.py --impl reference ...     # the FP64 CPU oracle on the host cores, same metric
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -28,10 +32,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PT-TEBD site-steps/s and TFLOP/s vs roofline, FP32-TC vs FP64 at <=1e-5 obs err"
 UNIT = "site-steps/s"
-DEFAULT_WORKLOAD = "xyz5_twobaths"
+DEFAULT_WORKLOAD = "xy21_allbaths"
+SECONDARY_WORKLOAD = "xyz5_twobaths"
 SM_COUNT = 152
-JACOBI_DRAM_BYTES_PER_LAUNCH = 1378048 + 174848   # bytes, ncu capture of the current k_jacobi_grid
-FP64_FLOPS_PER_CLK_PER_SM = 4.0       # 2 DFMA / clk / SM: 1.25 TFLOP/s nominal at 2.07 GHz x 152 SMs
+FP64_FLOPS_PER_CLK_PER_SM = 4.0       # 2 DFMA / clk / SM: 1.26 TFLOP/s at 2.07 GHz x 152 SMs
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 
 
 def parse():
@@ -40,10 +45,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3", "tf32x1"])
+    ap.add_argument("--precision", default="bf16_ozaki",
+                    choices=["bf16_ozaki", "fp64", "tf32x3", "bf16x3", "tf32x1"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0)
+    # a smaller case of the same kernels (lower bond cap, smaller capacity buffers), for profiling
+    ap.add_argument("--chi-max", type=int, default=0)
+    ap.add_argument("--no-fp64-path", action="store_true")
     return ap.parse_args()
 
 
@@ -113,6 +124,34 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------------ algorithmic flops
+def svd_flops(mD, nD, k):
+    """SVD of an m x n complex D of numerical rank k (the pivoted QR's rank), Golub-Van Loan counts:
+    Householder QR to rank k, 4(4mnk - 2k^2(m+n) + 4k^3/3); the SVD of the n x k factor with both
+    singular-vector sets, 4(4n^2k + 8nk^2 + 9k^3); and U = D V, 8mnk (complex flops = 4 real)."""
+    m, n = max(mD, nD), min(mD, nD)
+    k = n if k <= 0 else min(k, n)
+    qr = 4.0 * (4.0 * m * n * k - 2.0 * k * k * (m + n) + 4.0 * k ** 3 / 3.0)
+    small = 4.0 * (4.0 * n * n * k + 8.0 * n * k * k + 9.0 * k ** 3)
+    return qr + small + 8.0 * m * n * k
+
+
+def svd_flops_full(mD, nD):
+    """The full-rank Golub-Van Loan count 4(4m^2n + 8mn^2 + 9n^3) x 4 (complex)."""
+    m, n = max(mD, nD), min(mD, nD)
+    return 4.0 * (4 * m * m * n + 8 * m * n * n + 9 * n ** 3)
+
+
+def log_flops(rec):
+    """SVD flops of every bond update of the window from the device bond log [K, 6, nb, 8]."""
+    mD, nD, k = rec[..., 0].astype(np.float64), rec[..., 1].astype(np.float64), rec[..., 2]
+    tot = full = 0.0
+    for m, n, kk in zip(mD.ravel(), nD.ravel(), k.ravel()):
+        if m > 0 and n > 0:
+            tot += svd_flops(m, n, int(kk))
+            full += svd_flops_full(m, n)
+    return tot, full
+
+
 def bond_sizes(chis, kaps, N):
     """(m_L, n_L, m_R, n_R, r_L, r_R, chi) of every bond for the given dims (App. A.2)."""
     out = []
@@ -124,29 +163,23 @@ def bond_sizes(chis, kaps, N):
     return out
 
 
-def svd_flops(m, n):
-    """Golub-Van Loan dense SVD count with U and V, 4m^2n + 8mn^2 + 9n^3, x4 for complex."""
-    if m < n:
-        m, n = n, m
-    return 4.0 * (4 * m * m * n + 8 * m * n * n + 9 * n ** 3)
-
-
-def step_flops(chis, kaps, N):
-    """Algorithmic flops of one step: 3 bond updates per bond (the O layers twice, E once, per
-    half step -> odd bonds 4x, even bonds 2x), each QR + theta + SVD + recovery, plus the PT layer."""
-    svd = other = theta = 0.0
+def step_flops_rest(chis, kaps, N):
+    """Algorithmic flops of one step outside the SVD: the outer-block QR/LQ (with explicit Q), theta
+    with the gate, the Gamma recovery (each bond update: odd bonds 4x, even bonds 2x per step), and
+    the PT site contractions."""
+    other = theta = 0.0
     for b, (mL, nL, mR, nR, rL, rR, chc) in enumerate(bond_sizes(chis, kaps, N)):
         reps = 4 if b % 2 == 0 else 2
-        mD, nD = 4 * rL, 4 * rR
-        f_svd = svd_flops(mD, nD)
-        f_qr = (16.0 * (mL * nL * nL - nL ** 3 / 3) if mL > nL else 0.0) + \
-               (16.0 * (nR * mR * mR - mR ** 3 / 3) if nR > mR else 0.0)
+        f_qr = (32.0 * (mL * nL * nL - nL ** 3 / 3) if mL > nL else 0.0) + \
+               (32.0 * (nR * mR * mR - mR ** 3 / 3) if nR > mR else 0.0)
         f_theta = 128.0 * rL * rR * chc + 2048.0 * rL * rR
         f_rec = 8.0 * (mL * rL * 4 * chc if mL > nL else 0) + 8.0 * (nR * rR * 4 * chc if nR > mR else 0)
-        svd += reps * f_svd
         other += reps * (f_qr + f_theta + f_rec)
         theta += reps * f_theta
-    return svd, other, theta
+    for n in range(N):
+        chl, chr_ = chis[n], chis[n + 1]
+        other += 8.0 * chl * chr_ * 4 * kaps[n] * 4 * kaps[n]
+    return other, theta
 
 
 # ------------------------------------------------------------------------ replicas across ranks
@@ -168,26 +201,56 @@ def aggregate(total_ms, site_steps_local, dist=None, device="cpu"):
     return work / (total_ms / 1e3), total_ms
 
 
+def traffic_record(kernel_src):
+    """DRAM bytes per launch of the dominant stage from a committed ncu capture, or None once the
+    kernel source has changed since that capture (the record carries the source's SHA-256)."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None, "no ncu capture recorded"
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+    except Exception:
+        return None, "unreadable capture record"
+    sha = {}
+    for f in rec.get("sources", []):
+        p = os.path.join(ROOT, "paper_2201_05529_gb300", "csrc", f)
+        sha[f] = hashlib.sha256(open(p, "rb").read()).hexdigest()[:16] if os.path.exists(p) else None
+    if any(sha[f] != rec.get("sha", {}).get(f) for f in sha) or not sha:
+        return None, "kernel changed since the ncu capture"
+    return rec.get("dram_bytes_per_launch"), rec.get("how", "")
+
+
 # ------------------------------------------------------------------------ our arm
-# kernels per bond layer on the default route: blocks, QR/LQ reductions, theta (FP64: one kernel;
-# fast path: two packs + the tcgen05 GEMM), pivoted QR, Jacobi, V_D scatter, U_D GEMM, U_D scale,
-# truncation, recovery; per step 5 more (site contraction, swap, the two readout kernels, step counter)
-LAUNCHES_PER_LAYER = {"fp64": 10, "fast": 12}
-
-
-def _timed_window(eng, K, stream, flush, torch, n_chains, clk=None):
+def _timed_window(eng, K, stream, flush, torch):
     """K single steps, each bracketed by CUDA events on the library's stream, L2 flushed between."""
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    dims = []
     torch.cuda.synchronize()
     for i in range(K):
         flush.fill_(float(i))
         ev[i][0].record(stream)
         eng.step(1)
         ev[i][1].record(stream)
-        dims.append([eng.get_dims(c) for c in range(n_chains)])   # synchronises; outside the events
     torch.cuda.synchronize()
-    return [a.elapsed_time(b) for a, b in ev], dims
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def _secondary(capi, pp, workload, torch, stream, flush, prec, W=5, K=20):
+    """The five-site two-bath chain (the previous headline): fast path and FP64 path on one window."""
+    w = workload(SECONDARY_WORKLOAD)
+    chains, mpos = pp.build_problem(w)
+    N = sum(c["N"] for c in chains)
+    out = {"workload": w.name, "window": f"steps {W}..{W + K} of {w.K}"}
+    hist = {}
+    for p in (prec, "fp64"):
+        e = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, precision=p, max_steps=w.K, use_graph=True)
+        e.set_observables([pp.pauli("z")])
+        e.step(W)
+        ms = _timed_window(e, K, stream, flush, torch)
+        hist[p], _ = e.read_history(W, K + 1)
+        e.destroy()
+        out[p] = {"value": N * K / (sum(ms) / 1e3), "ms_per_step": float(np.mean(ms))}
+    out["speedup_vs_fp64_path"] = out[prec]["value"] / out["fp64"]["value"]
+    out["max_sz_diff_vs_fp64_path"] = float(np.max(np.abs(hist[prec] - hist["fp64"])))
+    return out
 
 
 def run_ours(args, rank, world, local):
@@ -200,7 +263,7 @@ def run_ours(args, rank, world, local):
     pkg.build()
     capi = pkg.load()
     capi.use_torch_allocator(local)
-    w = workload(args.workload)
+    w = workload(args.workload) if args.chi_max <= 0 else workload(args.workload, chi_max=args.chi_max)
     chains, mpos = pp.build_problem(w)
     K, W = args.steps, args.warmup
     if W + K > w.K:
@@ -209,9 +272,9 @@ def run_ours(args, rank, world, local):
     site_steps_per_step = sum(c["N"] for c in chains)
     n_chains = len(chains)
 
-    def make(precision):
+    def make(precision, graph=True):
         e = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, precision=precision,
-                        max_steps=w.K, use_graph=True)
+                        max_steps=w.K, use_graph=graph)
         e.set_observables([Z])
         return e
 
@@ -225,96 +288,99 @@ def run_ours(args, rank, world, local):
     eng = make(args.precision)
     eng.step(W)
     eng.sync()
+    stage_eng = eng.clone()                  # the same state at step W, for the per-stage timing
     if world > 1:
         dist.barrier()
     with ClockSampler(local) as clk:
-        step_ms, dims = _timed_window(eng, K, stream, flush, torch, n_chains)
+        step_ms = _timed_window(eng, K, stream, flush, torch)
     if world > 1:
         dist.barrier()
     value, total_ms = aggregate(float(np.sum(step_ms)), site_steps_per_step * K,
                                 dist if world > 1 else None, device="cuda")
     eng.sync()
-    sweeps = eng.get_svd_sweeps()
+    launches_per_step = eng.step_kernels()
     hist_fast, _ = eng.read_history(W, K + 1)
+    blog, disc = eng.read_bond_log(W, K)
+    dims = [eng.get_dims(c) for c in range(n_chains)]
     eng.destroy()
-    fl_svd = fl_other = fl_theta = 0.0
-    for per_chain in dims:
-        for c, (chi, kap) in enumerate(per_chain):
-            s_, o_, t_ = step_flops(list(chi), list(kap), chains[c]["N"])
-            fl_svd += s_
-            fl_other += o_
-            fl_theta += t_
+    fl_svd, fl_svd_full = log_flops(blog)
+    fl_rest = fl_theta = 0.0
+    for c, (chi, kap) in enumerate(dims):
+        o_, t_ = step_flops_rest(list(chi), list(kap), chains[c]["N"])
+        fl_rest += o_ * K          # the window's last dims: an upper estimate for the earlier steps
+        fl_theta += t_ * K
 
-    # --- the plain FP64 GPU path on the same window (for the FP32-TC vs FP64 comparison)
+    # --- per-stage device time over the same window (eager launches with events, on the clone)
+    stage_eng.set_timing(True)
+    stage = np.zeros(9)
+    for i in range(K):
+        flush.fill_(float(i))
+        stage_eng.step(1)
+        stage += stage_eng.get_timing()
+    stage_eng.set_timing(False)
+    stage_eng.destroy()
+
+    # --- the plain FP64 GPU path on the same window (FP32-TC vs FP64)
     fp64 = None
-    if args.precision != "fp64":
-        k64 = K
+    if args.precision != "fp64" and not args.no_fp64_path:
         e64 = make("fp64")
         e64.step(W)
         e64.sync()
-        ms64, _ = _timed_window(e64, k64, stream, flush, torch, n_chains)
-        hist64, _ = e64.read_history(W, k64 + 1)
+        ms64 = _timed_window(e64, K, stream, flush, torch)
+        hist64, _ = e64.read_history(W, K + 1)
         e64.destroy()
-        fp64 = {"value": site_steps_per_step * k64 / (float(np.sum(ms64)) / 1e3),
-                "ms_per_step": float(np.mean(ms64)), "steps": k64,
-                "window": f"steps {W}..{W + k64} (the same steps as the fast path)",
-                "max_obs_diff_vs_fast_path": float(np.max(np.abs(hist64 - hist_fast[:k64 + 1])))}
+        d = np.abs(hist64 - hist_fast)
+        fp64 = {"value": site_steps_per_step * K / (float(np.sum(ms64)) / 1e3),
+                "ms_per_step": float(np.mean(ms64)), "steps": K,
+                "window": f"steps {W}..{W + K} (the same steps as the fast path)",
+                "max_sz_diff_vs_fast_path": float(np.max(d)),
+                "max_sz_diff_per_step": [float(x) for x in d.max(axis=(1, 2, 3))]}
 
-    # --- per-stage timing (eager launches with events) over the same window
-    eng = make(args.precision)
-    eng.step(W)
-    eng.sync()
-    eng.set_timing(True)
-    stage = np.zeros(9)
-    nk = K
-    for i in range(nk):
-        flush.fill_(float(i))
-        eng.step(1)
-        stage += eng.get_timing()
-    eng.set_timing(False)
-    eng.destroy()
-    stage /= nk
+    # --- roofline of the dominant stage: the bond SVD (pivoted QR, Jacobi sweeps, U = D V)
     n_layers = 6
     svd_ms = stage[3] + stage[7] + stage[8]
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp64_peak = SM_COUNT * FP64_FLOPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
-    achieved = (fl_svd / K / n_layers) / (svd_ms / n_layers / 1e3) / 1e12
-    kernel = ("bond SVD (FP64 in every mode): pivoted QR k_qrcp_grid, one-sided Jacobi on R^H "
-              "k_jacobi_grid<double>, U_D = D V_D / sigma k_mix_gemm")
+    achieved = (fl_svd / (K * n_layers)) / (svd_ms / K / n_layers / 1e3) / 1e12
+    traffic, tsrc = traffic_record(["qrcp.cu", "jacobi_grid.cu", "svd_gemm.cu"])
     mp = measured_peaks()
     src = ("MEASURED_PEAKS.json gives HBM copy and bf16 GEMM peaks only" if mp else "MEASURED_PEAKS.json absent")
-    roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                # DRAM read + write of one k_jacobi_grid launch on a full-size layer (step 16, two
-                # 256x256 bonds) from an ncu capture of this kernel version (profiles/)
-                "traffic": JACOBI_DRAM_BYTES_PER_LAUNCH,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one k_jacobi_grid launch "
-                                  "at step 16 (full-size layer); the matrices stay in L2 otherwise",
-                "work": "Golub-Van Loan SVD flops 4(4m^2n+8mn^2+9n^3) x4 (complex) per bond update",
+    sweeps = blog[..., 3]
+    roofline = {"bound": "alu", "kernel": "bond SVD, one launch chain per layer: pivoted QR stopping at D's noise "
+                                          "level (k_qrcp_cl / k_qrcp_grid), FP64 one-sided Jacobi sweeps on "
+                                          "B = R^H (k_jacobi_grid), U = D V (k_mix_gemm)",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "traffic": traffic, "traffic_source": tsrc,
+                "work": "Golub-Van Loan counts of the SVD of each m x n D of numerical rank k (the pivoted QR's "
+                        "rank, read from the device bond log): QR to rank k + SVD of the n x k factor + U = D V",
+                "work_tflop_window": fl_svd / 1e12,
+                "work_full_rank_tflop_window": fl_svd_full / 1e12,
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x median SM clock (of derived; "
                                + src + "; a DFMA probe measured 1.20 TFLOP/s)",
-                "svd_ms_per_launch": svd_ms / n_layers,
-                "svd_sweeps_last_step": {"fp64": [int(x) for x in sweeps[:, 0]],
-                                         "fp32": [int(x) for x in sweeps[:, 1]]},
-                "stage_ms_per_step": {"site": stage[0], "blocks_qr": stage[1], "theta": stage[2],
-                                      "svd_fp64": stage[3], "svd_fp32": stage[7], "svd_precond": stage[8],
-                                      "truncate": stage[4], "recover": stage[5], "readout": stage[6]}}
-
+                "svd_ms_per_launch": svd_ms / K / n_layers,
+                "fp64_sweeps_mean": float(np.mean(sweeps[sweeps > 0])) if np.any(sweeps > 0) else 0.0,
+                "fp32_sweeps_mean": float(np.mean(blog[..., 4][blog[..., 4] > 0])) if np.any(blog[..., 4] > 0) else 0.0,
+                "rank_over_n_mean": float(np.mean((blog[..., 2] / np.maximum(1, np.minimum(blog[..., 0], blog[..., 1])))
+                                                  [blog[..., 0] > 0])),
+                "stage_ms_per_step": {"site": stage[0] / K, "blocks_qr": stage[1] / K, "theta": stage[2] / K,
+                                      "svd_fp64_sweeps": stage[3] / K, "svd_fp32_sweeps": stage[7] / K,
+                                      "svd_precond": stage[8] / K, "truncate": stage[4] / K,
+                                      "recover": stage[5] / K, "readout": stage[6] / K}}
     if args.precision != "fp64" and stage[2] > 0:
-        # the tcgen05 theta GEMM against the TF32 (or bf16) tensor peak: measured bf16 x the nominal
-        # dense ratio (TF32 1.1 / bf16 2.25 PFLOP/s), or the fallback figure without the file
+        # theta + gate on the tensor cores (the dense contraction of the fast path)
         bf16 = float(mp["bf16_tflops"]) if mp and "bf16_tflops" in mp else 1900.0
         tpeak = bf16 * (1.1 / 2.25) if args.precision in ("tf32x3", "tf32x1") else bf16
-        tach = (fl_theta / K) / (stage[2] / 1e3) / 1e12
+        tach = (fl_theta / K) / (stage[2] / K / 1e3) / 1e12
         roofline["theta_tensor"] = {
-            "kernel": "k_tc_pack + k_tc_theta (tcgen05 3M complex GEMM, split pieces)", "bound": "tensor",
+            "kernel": "k_tc_pack + k_tc_theta (theta + gate as one tcgen05 GEMM, K = 4 chi)", "bound": "tensor",
             "achieved": tach, "peak": tpeak, "unit": "TFLOP/s", "frac": tach / tpeak,
             "work": "128 r^2 chi + 2048 r^2 per bond update (algorithmic, complex MAC = 8)",
-            "peak_source": ("of measured: bf16 GEMM burst x 1.1/2.25" if mp else "of fallback: 1.9 PF bf16 x 1.1/2.25")
-            if args.precision in ("tf32x3", "tf32x1") else ("of measured: bf16 GEMM burst" if mp else "of fallback")}
+            "peak_source": "of measured bf16 GEMM burst" + (" x 1.1/2.25" if "tf32" in args.precision else "")}
 
-    # --- end to end through the C ABI: host inputs -> init (H2D) -> W+K steps -> history (D2H)
+    # --- end to end through the C ABI: host inputs -> init (H2D) -> W + K steps -> history (D2H);
+    # the work counted is the K-step window's only, while the timed region also holds the init and
+    # the W warm-up steps: a lower bound on the window's end-to-end rate
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2 = make(args.precision)
@@ -328,61 +394,75 @@ def run_ours(args, rank, world, local):
         h2d += (c["gates_q"].nbytes + c["gates_h"].nbytes) if c["N"] > 1 else 0
     h2d += sum(P.nbytes for Ps in mpos for P in Ps)
     d2h = hist.nbytes + tr.nbytes
-    e2e = {"value": site_steps_per_step * (W + K) / (t1 - t0), "unit": UNIT,
-           "h2d_bytes_per_step": int(h2d / (W + K)), "d2h_bytes_per_step": int(d2h / (W + K)),
-           "window": f"init + steps 0..{W + K} + history read, all timed"}
-    path = "fp64" if args.precision == "fp64" else "fast"
-    gpu_launches = K * (6 * LAUNCHES_PER_LAYER[path] + 5)
+    e2e = {"value": site_steps_per_step * K / (t1 - t0), "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d / K), "d2h_bytes_per_step": int(d2h / K),
+           "window": f"steps {W}..{W + K} counted; timed: init (all host inputs to the device) + steps "
+                     f"0..{W + K} + the history read"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32 (tf32/bf16 TC) + f64",
+           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16 TC slices (fp32 acc) + f64",
            "data": "synthetic (seeded workload; PT-MPOs built on the host from the stated Ohmic baths)",
            "config": {"workload": w.name, "chains": n_chains, "N": [c["N"] for c in chains],
                       "dt": w.dt, "chi_max": w.chi_max, "kappa_max": w.kappa_max, "eps": w.eps,
                       "precision": args.precision, "window": f"steps {W}..{W + K} of {w.K}",
                       "l2": "flushed between timed steps (256 MiB write)",
                       "parallelism": f"{world} replicas" if world > 1 else "single GPU"},
-           "clocks": clocks, "roofline": roofline, "e2e": e2e, "gpu_launches": gpu_launches,
-           "algorithmic_tflops": (fl_svd + fl_other) / (total_ms / 1e3) / 1e12}
+           "clocks": clocks, "roofline": roofline, "e2e": e2e,
+           "gpu_launches": int(launches_per_step) * K,
+           "gpu_launches_per_step": int(launches_per_step),
+           "algorithmic_tflops": (fl_svd + fl_rest) / (total_ms / 1e3) / 1e12,
+           "max_discarded_weight": float(np.max(disc)) if disc.size else 0.0}
     if fp64 is not None:
         out["fp64_path"] = fp64
         out["speedup_vs_fp64_path"] = value / fp64["value"]
+    if not args.no_secondary and args.workload != SECONDARY_WORKLOAD:
+        out["secondary"] = _secondary(capi, pp, workload, torch, stream, flush, args.precision)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w, W, args.cpu_seconds, site_steps_per_step)
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     if world > 1:
         dist.destroy_process_group()
     return out
 
 
 # ------------------------------------------------------------------------ the oracle on the host
-def cpu_baseline(w, warm, seconds, site_steps_per_step):
-    """Time the FP64 oracle as it stands on the host cores: W untimed steps from t = 0, then as
-    many steps as fit in about `seconds` (at least one)."""
-    from oracle import problem as oprob, model, pttebd
+def _oracle_steps(w, seconds, max_steps):
+    """The FP64 oracle as it stands from t = 0: steps timed one by one until `seconds` have passed."""
+    from oracle import problem as oprob, pttebd
     cis = oprob.build_inputs(w)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    total_steps = 0
-    t_total = 0.0
-    for ci in cis:
-        m = pttebd.product_state(ci.rho0) if ci.init_mps is None else ci.init_mps.copy()
-        for k in range(1, warm + 1):
-            pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
+    done, t_all = 0, 0.0
+    states = [pttebd.product_state(ci.rho0) if ci.init_mps is None else ci.init_mps.copy() for ci in cis]
+    for k in range(1, max_steps + 1):
         t0 = time.perf_counter()
-        k = warm
-        while k < w.K:
-            k += 1
+        for ci, m in zip(cis, states):
             pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
-            total_steps += 1
-            if time.perf_counter() - t0 > seconds / max(1, len(cis)):
-                break
-        t_total += time.perf_counter() - t0
-        if len(cis) > 4 and t_total > seconds:
+        t_all += time.perf_counter() - t0
+        done = k
+        if t_all > seconds:
             break
-    n_sites_done = total_steps * (site_steps_per_step / len(cis))
-    return {"value": n_sites_done / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{total_steps} steps after {warm} warm-up steps of {w.name} "
-                      f"(numpy/LAPACK, {cores} host threads available)"}
+    return done, t_all, sum(ci.N for ci in cis)
+
+
+def cpu_baseline(w, seconds):
+    """The oracle as it stands on the host cores over the first steps of the trajectory (a bounded,
+    labelled per-step rate: these early steps are the cheapest, so the rate is an upper bound for the
+    GPU's window), plus the same with one BLAS thread."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    done, t_all, N = _oracle_steps(w, seconds, w.K)
+    out = {"value": N * done / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"steps 1..{done} of {w.name} from t = 0 (per-step rate of the first steps; numpy/LAPACK, "
+                     f"{cores} host threads available)"}
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; from workloads import workload; "
+            "d, t, n = bench._oracle_steps(workload(%r), %f, %d); print(json.dumps([d, t, n]))"
+            % (ROOT, w.name, seconds / 2, w.K))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        d1, t1, n1 = json.loads(r.stdout.strip().splitlines()[-1])
+        out["single_thread"] = {"value": n1 * d1 / t1, "cores": 1, "sample": f"steps 1..{d1}, one BLAS thread"}
+    except Exception as ex:          # reported, not fatal
+        out["single_thread"] = {"value": None, "error": str(ex)[:200]}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -395,30 +475,35 @@ def run_reference(args, rank, world):
     cis = oprob.build_inputs(w)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     site_steps = sum(ci.N for ci in cis)
-    # each "step" of the reference arm is one PT-TEBD step of the same trajectory (bounded: K steps)
-    ms = []
+    # the same trajectory: W untimed steps, then up to K timed steps within the time budget (each
+    # step is one PT-TEBD step of every chain; later steps cost more, so a cut window is cheaper)
     states = []
     for ci in cis:
         m = pttebd.product_state(ci.rho0) if ci.init_mps is None else ci.init_mps.copy()
         for k in range(1, W + 1):
             pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
         states.append(m)
-    t0 = time.perf_counter()
+    ms = []
+    t_all = 0.0
     for i in range(K):
         ts = time.perf_counter()
         for ci, m in zip(cis, states):
             pttebd.pt_step(m, W + i + 1, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
         ms.append((time.perf_counter() - ts) * 1e3)
-    t_all = time.perf_counter() - t0
-    value = site_steps * K / t_all
+        t_all += ms[-1] / 1e3
+        if t_all > args.ref_seconds:
+            break
+    done = len(ms)
+    value = site_steps * done / t_all
+    sample = (f"steps {W + 1}..{W + done} of {w.name} after {W} untimed steps"
+              + ("" if done == K else f" ({done} of the {K} requested within the {args.ref_seconds:.0f} s budget)"))
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-            "ms_per_step": t_all * 1e3 / K, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": t_all * 1e3 / done, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "impl": "reference",
             "data": "synthetic (seeded workload; PT-MPOs built by the oracle)",
             "config": {"workload": w.name, "chains": len(cis), "precision": "fp64 (numpy/LAPACK)",
-                       "window": f"steps {W}..{W + K} of {w.K}"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{K} steps after {W} warm-up steps of {w.name}"},
+                       "window": f"steps {W}..{W + done} of {w.K}", "steps_timed": done},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

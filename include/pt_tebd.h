@@ -94,6 +94,14 @@ typedef struct {
   int max_steps;                  /* history capacity when no PT-MPO bounds the run (0: 1024) */
   int max_sweeps;                 /* Jacobi sweep cap before PT_ERR_SVD_NOCONV (0: 60) */
   int use_graph;                  /* capture one step as a CUDA graph and replay it */
+  int autotune;                   /* 1: per bond layer, time the candidate kernels of the SVD's pivoted
+                                     QR and of the outer-block QR once, on a synthetic state at
+                                     capacity, and keep the fastest (0: a fixed default order) */
+  const char* tune_cache;         /* text file of tuned choices (read, appended), or NULL */
+  int force_route;                /* 0: tuned or default; else 1 + qr + 4 k2 for every layer, with qr
+                                     0 whole-GPU / 1 cluster shared-memory / 2 cluster global-memory
+                                     pivoted QR, k2 0 whole-GPU / 1 one-CTA-per-block outer QR
+                                     (PT_ERR_ARG where it does not fit) */
 } pt_options;
 
 /* Device memory hook: alloc(bytes, ctx) returns device memory or NULL; free(ptr, ctx). */
@@ -132,14 +140,40 @@ int pt_tebd_apply_local(pt_tebd_t h, int chain, int site, const double* op2x2, i
 /* State queries (synchronous): number of completed steps; bond dims [N+1] and augmented dims [N]
  * of one chain; lambda of one bond (up to cap doubles); log of the state's norm factor. */
 int pt_tebd_steps_done(pt_tebd_t h);
+/* Kernel launches of one step: the kernel nodes of the captured step graph (use_graph only). */
+int pt_tebd_step_kernels(pt_tebd_t h);
+/* The kernels each layer runs (the paper has no counterpart): out8 = [odd qr, odd k2, odd tuned,
+ * odd from cache, even qr, even k2, even tuned, even from cache] (routes as in pt_options);
+ * ms10 (may be NULL) = the tuner's timings per layer: 3 pivoted-QR and 2 outer-QR candidates (ms,
+ * -1 where not a candidate). */
+int pt_tebd_get_routes(pt_tebd_t h, int* out8, float* ms10);
+/* The tuner's cache file (the paper has no counterpart): one line per layer shape,
+ * "key<TAB>qr<TAB>k2<TAB>timings"; the last valid line of a key wins, malformed lines are ignored.
+ * lookup returns 1 and the choice if the key is present, 0 if not; store appends a line. No GPU
+ * needed. */
+int pt_tune_cache_lookup(const char* path, const char* key, int* qr, int* k2);
+int pt_tune_cache_store(const char* path, const char* key, int qr, int k2);
 int pt_tebd_get_dims(pt_tebd_t h, int chain, int* chi, int* kappa);
 int pt_tebd_get_lambda(pt_tebd_t h, int chain, int bond, double* out, int cap);
 int pt_tebd_get_lognorm(pt_tebd_t h, int chain, double* out);
 
 /* Jacobi sweeps of the most recent update of every bond (odd-layer bonds first, then even):
- * out[2i] = FP64 sweeps, out[2i+1] = FP32 sweeps (fast path; 0 otherwise); a negative count marks
- * a bond that hit max_sweeps. Writes min(cap, n_bonds) pairs; returns n_bonds. */
+ * out[2i] = FP64 sweeps (negative: the bond hit max_sweeps), out[2i+1] = the update's fault flags
+ * (1: theta + gate gave a NaN or an infinity, 2: a NaN singular value, 4: the kept singular values
+ * have norm zero; 0 normally). Writes min(cap, n_bonds) pairs; returns n_bonds. */
 int pt_tebd_get_svd_sweeps(pt_tebd_t h, int* out, int cap);
+
+/* Per-step log of every bond update (the bond dimensions over time that App. B.3 tracks, plus the
+ * SVD's work), for steps [first, first+count): out receives [count][6 layers][nb][10] ints, layers in
+ * step order O E O | O E O (O: bonds (1,2),(3,4),..., E: the others), bond b of the layer's list
+ * (chains in order, bonds left to right); nb = the larger list length, absent bonds all zero. Fields:
+ * 0 rows and 1 columns of D (0: skipped), 2 the pivoted QR's rank (0 on routes without it),
+ * 3 Jacobi sweeps (negative: the sweep cap was hit), 4 fault flags (as in pt_tebd_get_svd_sweeps),
+ * 5 the new bond dimension, 6 and 7 the augmented dimensions of the two sites, 8-9 the discarded
+ * weight ||sigma_discarded||_2 / sigma_max as a double. cap_ints bounds out. Synchronous; returns
+ * nb. A diagnostic: it also reads after a device status error (PT_ERR_NAN and the like), whose
+ * bond it shows; only a CUDA error fails it. */
+int pt_tebd_read_bond_log(pt_tebd_t h, int first, int count, int* out, size_t cap_ints);
 
 /* Copy the whole device state into a new handle (App. B.2: continue from the full augmented MPS). */
 int pt_tebd_clone(pt_tebd_t h, pt_tebd_t* out);

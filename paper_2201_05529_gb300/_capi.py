@@ -25,7 +25,8 @@ EXPORTS = [
     "pt_tebd_set_allocator", "pt_tebd_init", "pt_tebd_set_observables", "pt_tebd_step",
     "pt_tebd_observe", "pt_tebd_read_history", "pt_tebd_apply_local", "pt_tebd_steps_done",
     "pt_tebd_get_dims", "pt_tebd_get_lambda", "pt_tebd_get_lognorm", "pt_tebd_get_svd_sweeps",
-    "pt_tebd_clone",
+    "pt_tebd_clone", "pt_tebd_read_bond_log", "pt_tebd_step_kernels", "pt_tebd_get_routes",
+    "pt_tune_cache_lookup", "pt_tune_cache_store",
     "pt_tebd_sync", "pt_tebd_destroy", "pt_tebd_last_error", "pt_tebd_set_timing",
     "pt_tebd_get_timing", "pt_svd_scratch_bytes", "pt_svd_f64", "pt_svd_f64_noalloc",
     "pt_selftest_grid_barrier",
@@ -64,7 +65,14 @@ class MpoDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("chi_max", C.c_int), ("eps", C.c_double), ("multiplet_tol", C.c_double),
                 ("precision", C.c_int), ("max_steps", C.c_int), ("max_sweeps", C.c_int),
-                ("use_graph", C.c_int)]
+                ("use_graph", C.c_int), ("autotune", C.c_int), ("tune_cache", C.c_char_p),
+                ("force_route", C.c_int)]
+
+
+# the tuner's cache of kernel choices per layer shape (in-tree, next to the library)
+TUNE_CACHE = os.path.join(HERE, "_tune_cache.tsv")
+QR_ROUTES = {"grid": 0, "cluster_smem": 1, "cluster_global": 2}
+K2_ROUTES = {"grid": 0, "cta": 1}
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -80,11 +88,16 @@ lib.pt_tebd_observe.argtypes = [C.c_void_p, c_double_p, C.c_int, c_double_p, c_d
 lib.pt_tebd_read_history.argtypes = [C.c_void_p, C.c_int, C.c_int, c_double_p, c_double_p]
 lib.pt_tebd_apply_local.argtypes = [C.c_void_p, C.c_int, C.c_int, c_double_p, C.c_int]
 lib.pt_tebd_steps_done.argtypes = [C.c_void_p]
+lib.pt_tebd_step_kernels.argtypes = [C.c_void_p]
+lib.pt_tebd_get_routes.argtypes = [C.c_void_p, c_int_p, C.POINTER(C.c_float)]
+lib.pt_tune_cache_lookup.argtypes = [C.c_char_p, C.c_char_p, c_int_p, c_int_p]
+lib.pt_tune_cache_store.argtypes = [C.c_char_p, C.c_char_p, C.c_int, C.c_int]
 lib.pt_tebd_get_dims.argtypes = [C.c_void_p, C.c_int, c_int_p, c_int_p]
 lib.pt_tebd_get_lambda.argtypes = [C.c_void_p, C.c_int, C.c_int, c_double_p, C.c_int]
 lib.pt_tebd_get_lognorm.argtypes = [C.c_void_p, C.c_int, c_double_p]
 lib.pt_tebd_get_svd_sweeps.argtypes = [C.c_void_p, c_int_p, C.c_int]
 lib.pt_tebd_clone.argtypes = [C.c_void_p, C.POINTER(C.c_void_p)]
+lib.pt_tebd_read_bond_log.argtypes = [C.c_void_p, C.c_int, C.c_int, c_int_p, C.c_size_t]
 lib.pt_tebd_sync.argtypes = [C.c_void_p]
 lib.pt_tebd_destroy.argtypes = [C.c_void_p]
 lib.pt_tebd_last_error.argtypes = [C.c_void_p]
@@ -157,7 +170,7 @@ class Engine:
     def __init__(self, chains: Sequence[dict], pt_mpos: Sequence[Sequence[np.ndarray]], chi_max: int,
                  eps: float, precision: str = "fp64", multiplet_tol: float = 1e-12,
                  max_steps: int = 0, max_sweeps: int = 0, use_graph: bool = True, stream=None,
-                 _handle=None):
+                 autotune: bool = True, tune_cache: Optional[str] = TUNE_CACHE, route=None, _handle=None):
         self._keep = []
         self.h = C.c_void_p()
         self.n_chains = len(chains)
@@ -211,9 +224,15 @@ class Engine:
             mdescs[m].K = K
             mdescs[m].kappa = kap.ctypes.data_as(c_int_p)
             mdescs[m].P = ptrs
+        force = 0
+        if route is not None:                     # (qr route, outer-QR route) by name, for tests
+            force = 1 + QR_ROUTES[route[0]] + 4 * K2_ROUTES[route[1]]
+        cache = tune_cache.encode() if tune_cache else None
+        self._keep.append(cache)
         opt = Options(chi_max=int(chi_max), eps=float(eps), multiplet_tol=float(multiplet_tol),
                       precision=PRECISIONS[precision], max_steps=int(max_steps),
-                      max_sweeps=int(max_sweeps), use_graph=int(bool(use_graph)))
+                      max_sweeps=int(max_sweeps), use_graph=int(bool(use_graph)),
+                      autotune=int(bool(autotune)), tune_cache=cache, force_route=force)
         st = stream if stream is not None else current_stream_handle()
         rc = lib.pt_tebd_init(C.byref(self.h), descs, len(chains), mdescs, len(pt_mpos),
                               C.byref(opt), st)
@@ -251,6 +270,22 @@ class Engine:
     def steps_done(self):
         return _check(lib.pt_tebd_steps_done(self.h), self.h)
 
+    def routes(self):
+        """pt_tebd_get_routes: {'odd'|'even': (qr route, outer-QR route, tuned, from cache, timings)}."""
+        out = np.zeros(8, dtype=np.int32)
+        ms = np.zeros(10, dtype=np.float32)
+        _check(lib.pt_tebd_get_routes(self.h, out.ctypes.data_as(c_int_p), ms.ctypes.data_as(C.POINTER(C.c_float))),
+               self.h)
+        qn = {v: k for k, v in QR_ROUTES.items()}
+        kn = {v: k for k, v in K2_ROUTES.items()}
+        return {layer: (qn[int(out[4 * l])], kn[int(out[4 * l + 1])], bool(out[4 * l + 2]), bool(out[4 * l + 3]),
+                        [float(x) for x in ms[5 * l:5 * l + 5]])
+                for l, layer in enumerate(("odd", "even"))}
+
+    def step_kernels(self):
+        """pt_tebd_step_kernels: kernel launches per step (nodes of the captured step graph)."""
+        return _check(lib.pt_tebd_step_kernels(self.h), self.h)
+
     def get_dims(self, chain):
         N = self.N[chain]
         chi = np.zeros(N + 1, dtype=np.int32)
@@ -270,10 +305,20 @@ class Engine:
         return v.value
 
     def get_svd_sweeps(self, cap=4096):
-        """[(fp64 sweeps, fp32 sweeps)] of the latest update of every bond (odd layer first)."""
+        """[(Jacobi sweeps, fault flags)] of the latest update of every bond (odd layer first)."""
         out = np.zeros(2 * cap, dtype=np.int32)
         n = _check(lib.pt_tebd_get_svd_sweeps(self.h, out.ctypes.data_as(c_int_p), cap), self.h)
         return out[:2 * min(n, cap)].reshape(-1, 2)
+
+    def read_bond_log(self, first, count, nb_max=4096):
+        """pt_tebd_read_bond_log: ([count, 6, nb, 8] int fields 0-7, [count, 6, nb] discarded weight)."""
+        n_ints = count * 6 * nb_max * 10
+        buf = np.zeros(max(1, n_ints), dtype=np.int32)
+        nb = _check(lib.pt_tebd_read_bond_log(self.h, int(first), int(count), buf.ctypes.data_as(c_int_p),
+                                              n_ints), self.h)
+        rec = buf[:count * 6 * nb * 10].reshape(count, 6, nb, 10)
+        disc = np.ascontiguousarray(rec[..., 8:10]).view(np.float64)[..., 0]
+        return rec[..., :8].copy(), disc
 
     def sync(self):
         _check(lib.pt_tebd_sync(self.h), self.h)
@@ -338,3 +383,16 @@ def selftest_grid_barrier(withheld_block=-1, limit_ms=1.0):
     st = C.c_int(0)
     rc = lib.pt_selftest_grid_barrier(int(withheld_block), float(limit_ms), C.byref(st))
     return rc, st.value
+
+
+def tune_cache_lookup(path, key):
+    """pt_tune_cache_lookup: (qr, k2) of the last valid line of `key`, or None."""
+    qr, k2 = C.c_int(-1), C.c_int(-1)
+    rc = lib.pt_tune_cache_lookup(path.encode(), key.encode(), C.byref(qr), C.byref(k2))
+    _check(rc, None)
+    return (qr.value, k2.value) if rc == 1 else None
+
+
+def tune_cache_store(path, key, qr, k2):
+    """pt_tune_cache_store: append a choice for `key`."""
+    _check(lib.pt_tune_cache_store(path.encode(), key.encode(), int(qr), int(k2)), None)

@@ -42,6 +42,14 @@ enum : int {
   ST_TIMEOUT = 16,
 };
 
+// per-update fault flags of one bond (info[6], cleared by the layer's first kernel; the bond log
+// keeps them): which check raised ST_NAN for that bond
+enum : int {
+  FAULT_D_NONFINITE = 1,      // theta + gate produced a NaN or an infinity (the SVD was skipped)
+  FAULT_SIGMA_NAN = 2,        // a singular value came out NaN
+  FAULT_ZERO_NORM = 4,        // the kept singular values have norm zero or NaN at the truncation
+};
+
 // ---------------------------------------------------------------- engine tables (device)
 // Global site index s, global bond (lambda) index B. Chain c owns sites
 // [site0[c], site0[c] + N[c]) and lambdas [lam0[c], lam0[c] + N[c] + 1).
@@ -84,8 +92,8 @@ struct BondWork {
   double2* HH;             // Householder vectors, max(mL*nL, nR*mR)
   double2* A;              // [mD_cap * nD_cap]  D (or D^H) col-major, becomes U (or V)
   double2* V;              // [k_cap * k_cap]    right factor of the one-sided Jacobi
-  double* sig;             // [k_cap] singular values (unsorted)
-  double* aux;             // [k_cap] column norms scratch
+  double* sig;             // [max(k_cap, mR_cap)] singular values (unsorted); B_R^H reflector scalars
+  double* aux;             // [max(k_cap, nL_cap)] column norms scratch; B_L reflector scalars
   int* perm;               // [k_cap] perm[rank] = column
   void* TA;                // fast path: packed split planes of the theta operands (tc_theta.cu)
   void* TB;
@@ -95,7 +103,8 @@ struct BondWork {
   double2* Y64;            // [max(mD,nD)_cap * k_cap] QR workspace / product scratch
   int* qperm;              // [k_cap] column permutation of the pivoted QR
   int* info;               // [16] per-item: 0 mD, 1 nD, 2 transposed, 3 sweeps, 4-5 rotation counters,
-                           // 6 FP32 sweeps, 7 NaN flag of theta, 8 rank k of the pivoted QR
+                           // 6 fault flags of the update (FAULT_*), 7 NaN flag of theta, 8 rank k of
+                           // the pivoted QR, 10-11 the update's discarded weight (a double)
   int mL_cap, nL_cap, mR_cap, nR_cap, mD_cap, nD_cap, k_cap, pad2;
 };
 
@@ -105,3 +114,35 @@ struct SiteWork {
   int lam;                 // global lambda index of the bond left of the site
   int pad;
 };
+
+// ---------------------------------------------------------------- live dims of one bond update
+// B_L = [(l,a),(p,c)] is mL x nL, B_R = [(c,q),(b,r)] is mR x nR; the QR (LQ) reduction runs when
+// B_L (B_R) is taller (wider) than its inner dimension; D is mD x nD = 4 rL x 4 rR.
+struct BondDims {
+  int sL, sR, BL, BC, BR;
+  int chl, chc, chr, kL, kR;
+  int mL, nL, mR, nR;
+  bool qrL, lqR;
+  int rL, rR, mD, nD;
+};
+
+PT_DEV BondDims bond_dims(const Tables& T, const BondWork& W) {
+  BondDims d;
+  d.sL = W.site_l; d.sR = W.site_l + 1;
+  d.BL = W.lam_l; d.BC = W.lam_l + 1; d.BR = W.lam_l + 2;
+  d.chl = T.lam_chi[d.BL]; d.chc = T.lam_chi[d.BC]; d.chr = T.lam_chi[d.BR];
+  d.kL = T.site_kappa[d.sL]; d.kR = T.site_kappa[d.sR];
+  d.mL = d.chl * d.kL; d.nL = 4 * d.chc;
+  d.mR = 4 * d.chc; d.nR = d.kR * d.chr;
+  d.qrL = d.mL > d.nL;
+  d.lqR = d.nR > d.mR;
+  d.rL = d.qrL ? d.nL : d.mL;
+  d.rR = d.lqR ? d.mR : d.nR;
+  d.mD = 4 * d.rL; d.nD = 4 * d.rR;
+  return d;
+}
+
+PT_DEV bool bond_fits(const BondDims& d, const BondWork& W) {
+  return d.mL <= W.mL_cap && d.nL <= W.nL_cap && d.mR <= W.mR_cap && d.nR <= W.nR_cap &&
+         d.mD <= W.mD_cap && d.nD <= W.nD_cap;
+}

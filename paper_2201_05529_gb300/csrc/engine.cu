@@ -5,6 +5,8 @@
 // whole step -- three bond layers, the PT site layer, three bond layers, readout -- is one fixed
 // launch sequence that can be captured as a CUDA graph and replayed.
 #include <algorithm>
+#include <functional>
+#include <climits>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -65,6 +67,7 @@ struct pt_tebd {
   std::vector<int> lam_cap_h;
   std::vector<size_t> site_cap_h;
   std::vector<int> kcap_h;            // per site
+  std::vector<int> kap_init_h, chi_init_h;   // initial augmented and bond dims (restored after tuning)
   std::vector<int> site_mpo_h;        // per site (after fusion)
   int n_mpos = 0;                     // device PT-MPOs (after fusion)
   int K_limit = 0;
@@ -81,11 +84,18 @@ struct pt_tebd {
   int grid_blocks = 0;                // whole-GPU Jacobi: CTAs per launch (0: use the cluster kernel)
   int tiles_odd = 1, tiles_even = 1;  // fast path: theta + gate GEMM output tiles per layer (capacity)
   std::vector<int*> bond_info;        // per bond (odd list, then even list): its info words
-  bool mixed_svd = false;             // fast path: FP32 bulk sweeps + FP64 polish on D (PT_TEBD_SVD=mixed)
-  bool precond = true;                // QR-preconditioned Jacobi (PT_TEBD_PRECOND=0 disables)
-  int qr_cluster = 1;
-  int qr_smem_cluster = 0;            // >0: the pivoted QR runs in cluster shared memory
-  bool qr_grid_odd = false, qr_grid_even = false;   // the pivoted QR runs on the whole GPU
+  int qr_cluster = 1;                 // CTAs per matrix of the global-memory cluster pivoted QR
+  int qr_smem_cluster = 0;            // >0: the cluster shared-memory pivoted QR fits (CTAs per matrix)
+  bool qr_grid_odd = false, qr_grid_even = false;   // the whole-GPU pivoted QR fits the layer
+  bool hqr_odd = false, hqr_even = false;            // the whole-GPU outer-block QR/LQ fits the layer
+  // the kernels each layer runs (chosen by the autotuner, forced, or by the default order)
+  struct Route {
+    int qr = 2;      // pivoted QR of the SVD: 0 whole GPU, 1 cluster shared memory, 2 cluster global memory
+    int k2 = 1;      // outer-block QR/LQ: 0 whole GPU, 1 one CTA per block
+    float ms_qr[3] = {-1, -1, -1}, ms_k2[2] = {-1, -1};   // tuner timings (ms; -1: not a candidate)
+    bool tuned = false, cached = false;
+  } route_odd, route_even;
+  int tune_status = 0;                // device status word seen at the end of the tuning run
   int kcap_odd = 1, kcap_even = 1, mcap_odd = 1, mcap_even = 1;
   unsigned* d_sync3 = nullptr;        // grid barrier state
   int* d_cnt_odd = nullptr;           // per-item rotation counters
@@ -112,6 +122,9 @@ struct pt_tebd {
   static constexpr int MAX_OPS = 16;
 
   int steps_done = 0;
+  int* d_blog = nullptr;              // bond log [hist_cap][6][blog_nb][BOND_LOG_INTS]
+  int graph_kernels = 0;              // kernel nodes of the captured step graph
+  int blog_nb = 1;
   cudaGraphExec_t graph = nullptr;
   bool timing = false;
   double stage_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -208,13 +221,32 @@ void ev_end(pt_tebd* h, cudaEvent_t e) {
 }
 
 // ---------------------------------------------------------------- the step launch sequence
-void enqueue_layer(pt_tebd* h, const BondWork* work, int n) {
+// outer-block QR/LQ of a layer: 0 whole GPU (k_hqr_grid), 1 one CTA per block (k_householder)
+void enqueue_k2(pt_tebd* h, const BondWork* work, int n, int k2) {
+  if (k2 == 0) ptk::launch_hqr_grid(h->T, work, n, h->grid_blocks, h->d_sync3, h->stream);
+  else ptk::k_householder<<<dim3(n, 2), ptk::QR_THREADS_, 0, h->stream>>>(h->T, work, n);
+}
+
+// pivoted QR of the SVD: 0 whole GPU, 1 cluster shared memory, 2 cluster global memory; it stops at
+// D's noise level (FP64 rounding, or the sliced tensor-core product's) or after kmax reflectors
+void enqueue_qr(pt_tebd* h, const BondWork* work, int n, int qr, int kmax) {
+  const int kc = work == h->d_odd ? h->kcap_odd : h->kcap_even, mc = work == h->d_odd ? h->mcap_odd : h->mcap_even;
+  const double tau2 = h->opt.precision == PT_BF16_OZAKI ? 8.271806125530277e-25    // (2^-40)^2
+                                                        : 1.232595164407831e-32;   // (2^-53)^2
+  if (qr == 0) ptk::launch_qrcp_grid(work, n, h->grid_blocks, h->d_sync3, tau2, kmax, h->T.status, h->stream);
+  else
+    ptk::launch_qrcp_precondition(work, n, h->qr_cluster, qr == 1 ? h->qr_smem_cluster : 0, kc, mc, tau2, kmax,
+                                  h->T.status, h->stream);
+}
+
+void enqueue_layer(pt_tebd* h, const BondWork* work, int n, int layer) {
   if (n == 0) return;
   cudaStream_t s = h->stream;
   cudaEvent_t e = nullptr;
   ev_begin(h, 1, &e);
   ptk::k_build_blocks<<<dim3(h->gx_bond, n), 256, 0, s>>>(h->T, work, n);
-  ptk::k_householder<<<dim3(n, 2), ptk::QR_THREADS_, 0, s>>>(h->T, work, n);
+  const pt_tebd::Route& rt = work == h->d_odd ? h->route_odd : h->route_even;
+  enqueue_k2(h, work, n, rt.k2);
   ev_end(h, e);
   ev_begin(h, 2, &e);
   if (h->opt.precision == PT_FP64)
@@ -224,56 +256,48 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n) {
   ptk::k_nan_guard<<<(n + 127) / 128, 128, 0, s>>>(h->T, work, n);
   ev_end(h, e);
   int* cnt = work == h->d_odd ? h->d_cnt_odd : h->d_cnt_even;
-  if (h->grid_blocks > 0 && h->opt.precision != PT_FP64 && h->mixed_svd) {
-    ev_begin(h, 7, &e);
-    ptk::launch_mixed_fp32(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status, s);
-    ev_end(h, e);
-    ev_begin(h, 8, &e);
-    ptk::launch_mixed_reorth(work, n, work == h->d_odd ? h->kcap_odd : h->kcap_even,
-                             work == h->d_odd ? h->mcap_odd : h->mcap_even, s);
-    ev_end(h, e);
-    ev_begin(h, 3, &e);
-    ptk::launch_mixed_fp64(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status,
-                           std::max(1.1102230246251565e-16, std::min(5.9604644775390625e-8, 0.01 * h->opt.eps)), s);
-    ev_end(h, e);
-  } else if (h->grid_blocks > 0 && h->precond) {
+  if (h->grid_blocks > 0) {
     // QR-preconditioned FP64 Jacobi: pivoted QR, Jacobi on R^H, then V_D = P U', U_D = D V_D / sigma
     const int kc = work == h->d_odd ? h->kcap_odd : h->kcap_even, mc = work == h->d_odd ? h->mcap_odd : h->mcap_even;
     ev_begin(h, 8, &e);
-    if (work == h->d_odd ? h->qr_grid_odd : h->qr_grid_even)
-      ptk::launch_qrcp_grid(work, n, h->grid_blocks, h->d_sync3, h->T.status, s);
-    else
-      ptk::launch_qrcp_precondition(work, n, h->qr_cluster, h->qr_smem_cluster, kc, mc, h->T.status, s);
+    enqueue_qr(h, work, n, rt.qr, INT_MAX);
     ev_end(h, e);
     ev_begin(h, 3, &e);
-    ptk::launch_jacobi_grid(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status, s, 0, 1, 1,
-                            1.1102230246251565e-16, 3, /*on_b=*/1);
-    ev_end(h, e);
-    ev_begin(h, 8, &e);
-    ptk::launch_qrcp_finish(work, n, kc, mc, s);
+    // rotation threshold |cos(b_i, b_j)| > m u in FP64; the sliced fast path, whose D is accurate to
+    // ~1e-12 of its scale, stops its sweeps at |cos| <= 1e-9 (the last, refining sweeps of the
+    // quadratic convergence are below its own accuracy)
+    const double tol_scale = h->opt.precision == PT_BF16_OZAKI ? 9.007199254740992e6 /* 1e-9 / u */ : 0.0;
+    ptk::launch_jacobi_grid(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status, s, 1, 1,
+                            1.1102230246251565e-16, 3, /*on_b=*/1, /*with_v=*/0, tol_scale);
     ev_end(h, e);
   } else {
+    // no co-resident whole-GPU launch possible on this device: one thread-block cluster per matrix
     ev_begin(h, 3, &e);
-    if (h->grid_blocks > 0)
-      ptk::launch_jacobi_grid(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status, s);
-    else
-      ptk::launch_jacobi_cluster(work, n, work == h->d_odd ? h->cl_odd : h->cl_even, h->opt.max_sweeps,
-                                 h->T.status, s);
+    ptk::launch_jacobi_cluster(work, n, work == h->d_odd ? h->cl_odd : h->cl_even, h->opt.max_sweeps,
+                               h->T.status, s);
     ev_end(h, e);
   }
   ev_begin(h, 4, &e);
   ptk::k_truncate<<<(n + 63) / 64, 64, 0, s>>>(h->T, work, n, h->opt.chi_max, h->opt.eps,
                                                 h->opt.multiplet_tol);
   ev_end(h, e);
+  if (h->grid_blocks > 0) {
+    // the SVD's finish on the kept columns only: V_D = P U', U_D = D V_D / sigma
+    const int kc = work == h->d_odd ? h->kcap_odd : h->kcap_even, mc = work == h->d_odd ? h->mcap_odd : h->mcap_even;
+    ev_begin(h, 8, &e);
+    ptk::launch_qrcp_finish(work, n, kc, mc, h->T.lam_chi, s);
+    ev_end(h, e);
+  }
   ev_begin(h, 5, &e);
   ptk::k_recover<<<dim3(h->gx_bond, n), 256, 0, s>>>(h->T, work, n);
   ev_end(h, e);
+  ptk::k_bond_log<<<(n + 127) / 128, 128, 0, s>>>(h->T, work, n, layer, h->d_blog, h->hist_cap, h->blog_nb);
 }
 
-void enqueue_chain_half(pt_tebd* h) {
-  enqueue_layer(h, h->d_odd, h->n_odd);
-  enqueue_layer(h, h->d_even, h->n_even);
-  enqueue_layer(h, h->d_odd, h->n_odd);
+void enqueue_chain_half(pt_tebd* h, int first_layer) {
+  enqueue_layer(h, h->d_odd, h->n_odd, first_layer);
+  enqueue_layer(h, h->d_even, h->n_even, first_layer + 1);
+  enqueue_layer(h, h->d_odd, h->n_odd, first_layer + 2);
 }
 
 void enqueue_observe_history(pt_tebd* h) {
@@ -289,7 +313,7 @@ void enqueue_observe_history(pt_tebd* h) {
 }
 
 void enqueue_step(pt_tebd* h) {
-  enqueue_chain_half(h);
+  enqueue_chain_half(h, 0);
   if (h->n_site_work > 0) {
     cudaEvent_t e = nullptr;
     ev_begin(h, 0, &e);
@@ -299,7 +323,7 @@ void enqueue_step(pt_tebd* h) {
                                                                           h->n_site_work);
     ev_end(h, e);
   }
-  enqueue_chain_half(h);
+  enqueue_chain_half(h, 3);
   ptk::k_step_inc<<<1, 1, 0, h->stream>>>(h->T.step);
   enqueue_observe_history(h);
 }
@@ -326,6 +350,19 @@ int capture_graph(pt_tebd* h) {
   h->timing = t;
   cudaStreamDestroy(cap);
   if (e != cudaSuccess) return h->fail(PT_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  {
+    // kernel launches per step: the kernel nodes of the captured graph
+    size_t nn = 0;
+    h->graph_kernels = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+        for (auto nd : nodes) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++h->graph_kernels;
+        }
+    }
+  }
   e = cudaGraphInstantiate(&h->graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return h->fail(PT_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
@@ -403,6 +440,208 @@ HostMpo fuse(const HostMpo& in, const cplx* LP) {
   return out;
 }
 
+// ---------------------------------------------------------------- autotuner
+
+// For each bond layer the kernels of two stages have candidates: the pivoted QR of the SVD (whole
+// GPU / cluster shared memory / cluster global memory, as far as they fit) and the outer-block
+// QR/LQ (whole GPU / one CTA per block). The tuner times every candidate once on a synthetic state
+// at capacity (every Gamma and lambda at its capacity dims, seeded values), keeps the fastest, and
+// caches the choice in a text file (one line per layer shape: key, QR route, outer-QR route,
+// timings), keyed by GPU name, driver version, compute capability, precision and the layer's
+// capacities. A layer whose key is cached is not timed again.
+std::string tune_key(pt_tebd* h, const std::vector<BondWork>& v, int k_cap, int m_cap) {
+  int dev = 0, drv = 0;
+  cudaGetDevice(&dev);
+  cudaDriverGetVersion(&drv);
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, dev);
+  std::string name(prop.name);
+  for (auto& ch : name)
+    if (ch == ' ' || ch == '\t' || ch == '|') ch = '_';
+  long long cols = 0;
+  int mL = 0;
+  for (auto& W : v) {
+    cols += W.nL_cap + W.mR_cap;
+    mL = std::max(mL, std::max(W.mL_cap, W.nR_cap));
+  }
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s|drv%d|sm%d%d|p%d|n%zu|k%d|m%d|c%lld|b%d", name.c_str(), drv, prop.major,
+           prop.minor, (int)h->opt.precision, v.size(), k_cap, m_cap, cols, mL);
+  return buf;
+}
+
+bool cache_lookup(const char* path, const std::string& key, int* qr, int* k2) {
+  if (!path || !*path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[2048];
+  bool found = false;
+  while (fgets(line, sizeof line, f)) {
+    char* tab = strchr(line, '\t');
+    if (!tab) continue;                                  // malformed: ignored
+    if (std::string(line, tab - line) != key) continue;
+    int a = -1, b = -1;
+    if (sscanf(tab + 1, "%d\t%d", &a, &b) == 2 && a >= 0 && a <= 2 && b >= 0 && b <= 1) {
+      *qr = a;                                           // the last valid line of a key wins
+      *k2 = b;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void cache_store(const char* path, const std::string& key, const pt_tebd::Route& r) {
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s\t%d\t%d\tms_qr=%.4f,%.4f,%.4f\tms_k2=%.4f,%.4f\n", key.c_str(), r.qr, r.k2, r.ms_qr[0],
+          r.ms_qr[1], r.ms_qr[2], r.ms_k2[0], r.ms_k2[1]);
+  fclose(f);
+}
+
+float time_once(pt_tebd* h, const std::function<void()>& launch) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, h->stream);
+  launch();
+  cudaEventRecord(b, h->stream);
+  cudaEventSynchronize(b);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms;
+}
+
+int tune_layer(pt_tebd* h, const BondWork* work, int n, const std::vector<BondWork>& v, pt_tebd::Route& r) {
+  const bool odd = work == h->d_odd;
+  const int kc = odd ? h->kcap_odd : h->kcap_even, mc = odd ? h->mcap_odd : h->mcap_even;
+  const std::string key = tune_key(h, v, kc, mc);
+  int qr = r.qr, k2 = r.k2;
+  if (cache_lookup(h->opt.tune_cache, key, &qr, &k2)) {
+    const bool qr_ok = qr == 2 || (qr == 1 && h->qr_smem_cluster > 0) || (qr == 0 && (odd ? h->qr_grid_odd : h->qr_grid_even));
+    const bool k2_ok = k2 == 1 || (odd ? h->hqr_odd : h->hqr_even);
+    if (qr_ok && k2_ok) {
+      r.qr = qr;
+      r.k2 = k2;
+      r.cached = true;
+      return PT_OK;
+    }
+  }
+  cudaStream_t s = h->stream;
+  // outer-block QR candidates (each on freshly built blocks; the faster of two runs)
+  std::vector<int> k2c{1};
+  if (odd ? h->hqr_odd : h->hqr_even) k2c.insert(k2c.begin(), 0);
+  for (int c : k2c) {
+    float best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep)
+      best = std::min(best, time_once(h, [&] {
+                        ptk::k_build_blocks<<<dim3(h->gx_bond, n), 256, 0, s>>>(h->T, work, n);
+                        enqueue_k2(h, work, n, c);
+                      }));
+    r.ms_k2[c] = best;
+  }
+  r.k2 = k2c[0];
+  for (int c : k2c)
+    if (r.ms_k2[c] < r.ms_k2[r.k2]) r.k2 = c;
+  // D of the synthetic state, then the pivoted-QR candidates on it (a 128-reflector prefix each;
+  // every candidate reads D and writes only its own workspace)
+  ptk::k_build_blocks<<<dim3(h->gx_bond, n), 256, 0, s>>>(h->T, work, n);
+  enqueue_k2(h, work, n, r.k2);
+  if (h->opt.precision == PT_FP64)
+    ptk::k_theta_gate<<<dim3(h->gx_bond, n), 128, 0, s>>>(h->T, work, n);
+  else
+    ptk::launch_tc_theta(h->T, work, n, odd ? h->tiles_odd : h->tiles_even, (int)h->opt.precision, s);
+  std::vector<int> qrc{2};
+  if (h->qr_smem_cluster > 0) qrc.insert(qrc.begin(), 1);
+  if (odd ? h->qr_grid_odd : h->qr_grid_even) qrc.insert(qrc.begin(), 0);
+  for (int c : qrc) {
+    float best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep)
+      best = std::min(best, time_once(h, [&] { enqueue_qr(h, work, n, c, std::min(kc, 128)); }));
+    r.ms_qr[c] = best;
+  }
+  r.qr = qrc[0];
+  for (int c : qrc)
+    if (r.ms_qr[c] < r.ms_qr[r.qr]) r.qr = c;
+  r.tuned = true;
+  int rc = check_cuda(h, "autotune");
+  if (rc == PT_OK) cache_store(h->opt.tune_cache, key, r);
+  return rc;
+}
+
+// ---------------------------------------------------------------- initial state
+// Gamma and lambda of the initial augmented MPS (product state or the caller's gamma0/lambda0)
+void upload_initial_gamma_lambda(pt_tebd* h) {
+  for (int c = 0; c < (int)h->chains.size(); ++c) {
+    HostChain& hc = h->chains[c];
+    for (int n = 0; n < hc.N; ++n) {
+      const int s = h->site0[c] + n;
+      std::vector<cplx> g;
+      if (hc.gamma0.empty()) g.assign(hc.rho0.begin() + 4 * n, hc.rho0.begin() + 4 * n + 4);
+      else g = hc.gamma0[n];
+      cudaMemcpyAsync(h->gam_a[s], g.data(), sizeof(cplx) * g.size(), cudaMemcpyHostToDevice, h->stream);
+    }
+    for (int b = 0; b <= hc.N; ++b) {
+      const int B = h->lam0[c] + b;
+      std::vector<double> l = hc.lambda0.empty() ? std::vector<double>{1.0} : hc.lambda0[b];
+      cudaMemcpyAsync(h->lam_buf[B], l.data(), sizeof(double) * l.size(), cudaMemcpyHostToDevice, h->stream);
+    }
+  }
+}
+
+// the route of every layer: forced (tests), tuned (timed once, cached), or the default order; the
+// tuning runs on a synthetic state at capacity, after which the initial state is restored
+int choose_routes(pt_tebd* h, const std::vector<BondWork>& odd, const std::vector<BondWork>& even) {
+  if (h->opt.force_route > 0) {
+    const int qr = (h->opt.force_route - 1) % 4, k2 = (h->opt.force_route - 1) / 4;
+    auto apply = [&](pt_tebd::Route& r, bool qr_grid, bool hqr) {
+      const bool ok = (qr == 2 || (qr == 1 && h->qr_smem_cluster > 0) || (qr == 0 && qr_grid)) &&
+                      (k2 == 1 || (k2 == 0 && hqr));
+      if (ok) {
+        r.qr = qr;
+        r.k2 = k2;
+      }
+      return ok;
+    };
+    if (qr > 2 || k2 > 1 || !apply(h->route_odd, h->qr_grid_odd, h->hqr_odd) ||
+        !apply(h->route_even, h->qr_grid_even, h->hqr_even))
+      return h->fail(PT_ERR_ARG, "force_route: that route does not fit this problem");
+    return PT_OK;
+  }
+  if (!h->opt.autotune || h->grid_blocks <= 0) return PT_OK;
+  // synthetic state at capacity
+  Tables& T = h->T;
+  cudaMemcpyAsync(T.site_kappa, h->kcap_h.data(), sizeof(int) * h->n_sites, cudaMemcpyHostToDevice, h->stream);
+  cudaMemcpyAsync(T.lam_chi, h->lam_cap_h.data(), sizeof(int) * h->n_lams, cudaMemcpyHostToDevice, h->stream);
+  ptk::k_tune_fill<<<4 * 152, 256, 0, h->stream>>>(T, h->n_sites, h->n_lams, 20220113u);
+  int rc = check_cuda(h, "autotune fill");
+  if (rc == PT_OK && h->n_odd > 0) rc = tune_layer(h, h->d_odd, h->n_odd, odd, h->route_odd);
+  if (rc == PT_OK && h->n_even > 0) rc = tune_layer(h, h->d_even, h->n_even, even, h->route_even);
+  // the synthetic run must not have tripped a device check; if it did, its timings are meaningless
+  cudaMemcpyAsync(&h->tune_status, T.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  if (h->tune_status != 0) {
+    auto defaults = [&](pt_tebd::Route& r, bool qr_grid, bool hqr) {
+      r.qr = qr_grid ? 0 : (h->qr_smem_cluster > 0 ? 1 : 2);
+      r.k2 = hqr ? 0 : 1;
+      r.tuned = false;
+    };
+    defaults(h->route_odd, h->qr_grid_odd, h->hqr_odd);
+    defaults(h->route_even, h->qr_grid_even, h->hqr_even);
+  }
+  // back to the initial state
+  upload_initial_gamma_lambda(h);
+  cudaMemcpyAsync(T.site_kappa, h->kap_init_h.data(), sizeof(int) * h->n_sites, cudaMemcpyHostToDevice, h->stream);
+  cudaMemcpyAsync(T.lam_chi, h->chi_init_h.data(), sizeof(int) * h->n_lams, cudaMemcpyHostToDevice, h->stream);
+  cudaMemsetAsync(T.lam_lognorm, 0, sizeof(double) * h->n_lams, h->stream);
+  cudaMemsetAsync(T.step, 0, sizeof(int), h->stream);
+  cudaMemsetAsync(T.status, 0, sizeof(int), h->stream);
+  return rc != PT_OK ? rc : check_cuda(h, "autotune restore");
+}
+
 // ---------------------------------------------------------------- build the device state
 int build(pt_tebd* h) {
   const int C = (int)h->chains.size();
@@ -462,7 +701,10 @@ int build(pt_tebd* h) {
   h->site_mpo_h.assign(h->n_sites, -1);
   h->lam_cap_h.assign(h->n_lams, 1);
   h->site_cap_h.assign(h->n_sites, 0);
-  std::vector<int> kap_init(h->n_sites, 1), chi_init(h->n_lams, 1);
+  std::vector<int>& kap_init = h->kap_init_h;
+  std::vector<int>& chi_init = h->chi_init_h;
+  kap_init.assign(h->n_sites, 1);
+  chi_init.assign(h->n_lams, 1);
   const double BIG = 1e9;
   for (int c = 0; c < C; ++c) {
     HostChain& hc = h->chains[c];
@@ -524,21 +766,7 @@ int build(pt_tebd* h) {
     maxchi = std::max(maxchi, h->lam_cap_h[B]);
   }
   // initial state
-  for (int c = 0; c < C; ++c) {
-    HostChain& hc = h->chains[c];
-    for (int n = 0; n < hc.N; ++n) {
-      const int s = h->site0[c] + n;
-      std::vector<cplx> g;
-      if (hc.gamma0.empty()) g.assign(hc.rho0.begin() + 4 * n, hc.rho0.begin() + 4 * n + 4);
-      else g = hc.gamma0[n];
-      cudaMemcpyAsync(h->gam_a[s], g.data(), sizeof(cplx) * g.size(), cudaMemcpyHostToDevice, h->stream);
-    }
-    for (int b = 0; b <= hc.N; ++b) {
-      const int B = h->lam0[c] + b;
-      std::vector<double> l = hc.lambda0.empty() ? std::vector<double>{1.0} : hc.lambda0[b];
-      cudaMemcpyAsync(h->lam_buf[B], l.data(), sizeof(double) * l.size(), cudaMemcpyHostToDevice, h->stream);
-    }
-  }
+  upload_initial_gamma_lambda(h);
 
   // PT-MPOs and caps
   std::vector<int> mK(h->n_mpos), kap_off(h->n_mpos), P_off(h->n_mpos), cap_off(h->n_mpos);
@@ -640,8 +868,12 @@ int build(pt_tebd* h) {
       W.HH = (double2*)h->dalloc(sizeof(double2) * (qls + qrs));
       W.A = (double2*)h->dalloc(sizeof(double2) * as);
       W.V = (double2*)h->dalloc(sizeof(double2) * vs);
-      W.sig = (double*)h->dalloc(sizeof(double) * W.k_cap);
-      W.aux = (double*)h->dalloc(sizeof(double) * W.k_cap);
+      // sig and aux: singular values and the pivoted QR's column norms (k_cap), and the whole-GPU
+      // outer-block QR's reflector scalars (n_L of B_L in aux, m_R of B_R^H in sig): on a chain's
+      // edge bonds 4 chi_c exceeds k_cap
+      const size_t sa = (size_t)std::max(W.k_cap, std::max(W.nL_cap, W.mR_cap));
+      W.sig = (double*)h->dalloc(sizeof(double) * sa);
+      W.aux = (double*)h->dalloc(sizeof(double) * sa);
       W.perm = (int*)h->dalloc(sizeof(int) * W.k_cap);
       W.info = (int*)h->dalloc(sizeof(int) * 16);
       if (!W.QL || !W.RL || !W.QR || !W.LR || !W.HH || !W.A || !W.V || !W.sig || !W.aux || !W.perm || !W.info)
@@ -687,8 +919,6 @@ int build(pt_tebd* h) {
     };
     h->tiles_odd = tiles(odd);
     h->tiles_even = tiles(even);
-    const char* sv = getenv("PT_TEBD_SVD");
-    h->mixed_svd = sv && std::string(sv) == "mixed";
   }
   {
     auto dims = [&](const std::vector<BondWork>& v, int* kc, int* mc) {
@@ -699,26 +929,19 @@ int build(pt_tebd* h) {
     };
     dims(odd, &h->kcap_odd, &h->mcap_odd);
     dims(even, &h->kcap_even, &h->mcap_even);
-    const char* pc = getenv("PT_TEBD_PRECOND");
-    h->precond = !(pc && std::string(pc) == "0");
     int k = std::max(h->kcap_odd, h->kcap_even);
     h->qr_cluster = ptk::qrcp_cluster_size(std::max(1, std::min(16, (k + 31) / 32)),
                                            std::max(h->mcap_odd, h->mcap_even), k);
-    const char* qv = getenv("PT_TEBD_QR");
-    if (!(qv && std::string(qv) == "global"))
-      h->qr_smem_cluster = ptk::qrcp_smem_cluster(std::max(h->mcap_odd, h->mcap_even), k);
+    h->qr_smem_cluster = ptk::qrcp_smem_cluster(std::max(h->mcap_odd, h->mcap_even), k);
   }
-  // bond SVDs: whole-GPU cooperative kernel by default; PT_TEBD_JACOBI=cluster selects one
-  // thread-block cluster per matrix instead
-  const char* jv = getenv("PT_TEBD_JACOBI");
-  const bool want_cluster = jv && std::string(jv) == "cluster";
-  h->grid_blocks = (!want_cluster && std::max(h->n_odd, h->n_even) <= 1024) ? ptk::jacobi_grid_blocks() : 0;
+  // bond SVDs: the whole-GPU cooperative kernels when the device can co-schedule them, else one
+  // thread-block cluster per matrix
+  h->grid_blocks = std::max(h->n_odd, h->n_even) <= 1024 ? ptk::jacobi_grid_blocks() : 0;
   {
-    // pivoted QR on the whole GPU where the layer's columns fit one per warp (PT_TEBD_QR=cluster or
-    // =global selects the cluster shared-memory or the global-memory kernel)
-    const char* qv = getenv("PT_TEBD_QR");
-    const bool qr_any = !(qv && (std::string(qv) == "cluster" || std::string(qv) == "global"));
-    const bool ok = qr_any && h->grid_blocks > 0 && ptk::qrcp_grid_ok();
+    // which kernels fit each layer: the whole-GPU pivoted QR where the layer's columns fit one per
+    // warp; the cluster shared-memory one where a matrix fits 200 KB per CTA; the global-memory one
+    // always; the whole-GPU outer-block QR where every block's columns fit the CTAs' share
+    const bool ok = h->grid_blocks > 0 && ptk::qrcp_grid_ok();
     auto fits = [&](const std::vector<BondWork>& v, int mc) {
       int tot = 0;
       for (auto& W : v) tot += W.k_cap;
@@ -726,6 +949,23 @@ int build(pt_tebd* h) {
     };
     h->qr_grid_odd = fits(odd, h->mcap_odd);
     h->qr_grid_even = fits(even, h->mcap_even);
+    // the outer-block reductions: whole GPU when every block's columns fit the CTAs' share
+    const bool hok = h->grid_blocks > 0 && ptk::hqr_grid_ok();
+    auto hfits = [&](const std::vector<BondWork>& v) {
+      long long cols = 0;
+      for (auto& W : v) cols += W.nL_cap + W.mR_cap;
+      return hok && !v.empty() && cols < (1LL << 30) &&
+             ptk::hqr_grid_fits((int)cols, 2 * (int)v.size(), h->grid_blocks);
+    };
+    h->hqr_odd = hfits(odd);
+    h->hqr_even = hfits(even);
+    // default order (no tuning): whole GPU, then cluster shared memory, then cluster global memory
+    auto defaults = [&](pt_tebd::Route& r, bool qr_grid, bool hqr) {
+      r.qr = qr_grid ? 0 : (h->qr_smem_cluster > 0 ? 1 : 2);
+      r.k2 = hqr ? 0 : 1;
+    };
+    defaults(h->route_odd, h->qr_grid_odd, h->hqr_odd);
+    defaults(h->route_even, h->qr_grid_even, h->hqr_even);
   }
   h->d_sync3 = (unsigned*)h->dalloc(sizeof(unsigned) * 4);
   h->d_cnt_odd = (int*)h->dalloc(sizeof(int) * 2 * std::max(1, h->n_odd));
@@ -758,6 +998,13 @@ int build(pt_tebd* h) {
   h->d_obs_now = (double2*)h->dalloc(sizeof(double2) * (size_t)C * h->n_max * pt_tebd::MAX_OPS);
   h->d_tr_now = (double2*)h->dalloc(sizeof(double2) * C);
   h->hist_cap = h->K_limit + 1;
+  h->blog_nb = std::max(1, std::max(h->n_odd, h->n_even));
+  {
+    const size_t nlog = (size_t)h->hist_cap * 6 * h->blog_nb * ptk::BOND_LOG_INTS;
+    h->d_blog = (int*)h->dalloc(sizeof(int) * nlog);
+    if (!h->d_blog) return h->fail(PT_ERR_OOM, "bond log");
+    cudaMemsetAsync(h->d_blog, 0, sizeof(int) * nlog, h->stream);
+  }
   if (!h->d_Lbuf || !h->d_Rbuf || !h->d_ops_now || !h->d_obs_now || !h->d_tr_now)
     return h->fail(PT_ERR_OOM, "readout buffers");
   {
@@ -776,6 +1023,10 @@ int build(pt_tebd* h) {
     h->d_moff = upload(h, moff);
     if (!h->d_Mbuf || !h->d_moff) return h->fail(PT_ERR_OOM, "readout buffers");
     h->gx_m = (int)std::min<size_t>(64, (mx + 255) / 256);
+  }
+  {
+    const int rc = choose_routes(h, odd, even);
+    if (rc != PT_OK) return rc;
   }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "init");
   return check_cuda(h, "init");
@@ -943,6 +1194,19 @@ int pt_tebd_read_history(pt_tebd_t h, int first, int count, double* out, double*
   return read_status(h);
 }
 
+int pt_tebd_read_bond_log(pt_tebd_t h, int first, int count, int* out, size_t cap_ints) {
+  if (!h || first < 0 || count < 0 || first + count > h->hist_cap || (count > 0 && !out)) return PT_ERR_ARG;
+  const size_t per = (size_t)6 * h->blog_nb * ptk::BOND_LOG_INTS;
+  if ((size_t)count * per > cap_ints) return h->fail(PT_ERR_ARG, "read_bond_log: output buffer too small");
+  if (count > 0)
+    cudaMemcpyAsync(out, h->d_blog + (size_t)first * per, sizeof(int) * per * count, cudaMemcpyDeviceToHost,
+                    h->stream);
+  // a diagnostic: readable after a device error (the log shows which bond raised it), so only a
+  // CUDA error fails here
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "read_bond_log");
+  return h->blog_nb;
+}
+
 int pt_tebd_apply_local(pt_tebd_t h, int chain, int site, const double* op2x2, int side) {
   if (!h || chain < 0 || chain >= h->n_chains || site < 0 || site >= h->chains[chain].N || !op2x2 ||
       (side != 0 && side != 1))
@@ -965,6 +1229,43 @@ int pt_tebd_apply_local(pt_tebd_t h, int chain, int site, const double* op2x2, i
 }
 
 int pt_tebd_steps_done(pt_tebd_t h) { return h ? h->steps_done : PT_ERR_ARG; }
+
+int pt_tebd_get_routes(pt_tebd_t h, int* out8, float* ms10) {
+  if (!h || !out8) return PT_ERR_ARG;
+  const pt_tebd::Route* r[2] = {&h->route_odd, &h->route_even};
+  for (int l = 0; l < 2; ++l) {
+    out8[4 * l + 0] = r[l]->qr;
+    out8[4 * l + 1] = r[l]->k2;
+    out8[4 * l + 2] = r[l]->tuned ? 1 : 0;
+    out8[4 * l + 3] = r[l]->cached ? 1 : 0;
+    if (ms10) {
+      for (int i = 0; i < 3; ++i) ms10[5 * l + i] = r[l]->ms_qr[i];
+      for (int i = 0; i < 2; ++i) ms10[5 * l + 3 + i] = r[l]->ms_k2[i];
+    }
+  }
+  return PT_OK;
+}
+
+int pt_tune_cache_lookup(const char* path, const char* key, int* qr, int* k2) {
+  if (!path || !key || !qr || !k2) return PT_ERR_ARG;
+  return cache_lookup(path, key, qr, k2) ? 1 : 0;
+}
+
+int pt_tune_cache_store(const char* path, const char* key, int qr, int k2) {
+  if (!path || !key || qr < 0 || qr > 2 || k2 < 0 || k2 > 1 || strchr(key, '\t') || strchr(key, '\n'))
+    return PT_ERR_ARG;
+  pt_tebd::Route r;
+  r.qr = qr;
+  r.k2 = k2;
+  cache_store(path, key, r);
+  return PT_OK;
+}
+
+int pt_tebd_step_kernels(pt_tebd_t h) {
+  if (!h) return PT_ERR_ARG;
+  if (!h->graph) return h->fail(PT_ERR_ARG, "step_kernels: the handle has no captured step graph");
+  return h->graph_kernels;
+}
 
 int pt_tebd_get_dims(pt_tebd_t h, int chain, int* chi, int* kappa) {
   if (!h || chain < 0 || chain >= h->n_chains) return PT_ERR_ARG;
@@ -1057,7 +1358,7 @@ int pt_tebd_get_svd_sweeps(pt_tebd_t h, int* out, int cap) {
     cudaMemcpyAsync(buf.data(), h->bond_info[i], sizeof(int) * 8, cudaMemcpyDeviceToHost, h->stream);
     cudaStreamSynchronize(h->stream);
     out[2 * i] = buf[3];
-    out[2 * i + 1] = buf[6];
+    out[2 * i + 1] = buf[6];         // the update's fault flags
   }
   int rc = read_status(h);
   return rc == PT_OK ? (int)h->bond_info.size() : rc;

@@ -35,17 +35,14 @@ __device__ __forceinline__ R wsumd(R v) {
 }
 
 template <typename R> struct Cx;
+// A: the matrix on D's shape; B: the matrix B = R^H of the pivoted QR (on_b); V: the right factor
+// (the sweeps are written for a real type R; the path instantiates them in FP64)
 template <> struct Cx<double> {
   using T = double2;
   static constexpr double EPS = 1.1102230246251565e-16;
   __device__ static T* A(const BondWork& W) { return W.A; }
+  __device__ static T* B(const BondWork& W) { return W.G64; }
   __device__ static T* V(const BondWork& W) { return W.V; }
-};
-template <> struct Cx<float> {
-  using T = float2;
-  static constexpr float EPS = 5.9604644775390625e-8f;
-  __device__ static T* A(const BondWork& W) { return W.A32; }
-  __device__ static T* V(const BondWork& W) { return W.V32; }
 };
 
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
@@ -82,7 +79,7 @@ template <typename R>
 __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R>::T* V, double* nrm, int Ma,
                                              int Na, int i, int j, double fro, double floor_eps, int grp, int gw,
                                              int lane, R (*s_part)[GROUP_WARPS][4], R (*s_rot)[8], int* cnt_slot,
-                                             bool with_v, int* stamp, int g_round, int skip_before) {
+                                             bool with_v, int* stamp, int g_round, int skip_before, R tol) {
   using C2 = typename Cx<R>::T;
   const R eps = Cx<R>::EPS;
   if (i > j) { const int tt = i; i = j; j = tt; }
@@ -139,7 +136,6 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
       gi += s_part[grp][k][1];
     }
     const R g2 = gr * gr + gi * gi;
-    const R tol = (R)Ma * eps;
     const R fl2 = (R)(floor_eps * floor_eps * fro);
     // rotate unless |gamma| <= tol sqrt(alpha beta), or a column is at the noise floor
     // (|a|^2 <= floor_eps^2 ||A||_F^2: such columns cannot become orthogonal relative to
@@ -234,15 +230,19 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
   }
 }
 
-// One-sided Jacobi over all matrices of a layer. R = double: FP64 on W.A / W.V (the FP64 path, and
-// the polishing sweeps of the fast path); R = float: FP32 on W.A32 / W.V32 (the fast path's bulk
-// sweeps). init_v: start from V = I (else from the V already stored). finalize: write sigma, the
-// normalised left vectors and the order. floor_eps: unit roundoff that sets the noise floor.
+// One-sided Jacobi over all matrices of a layer in FP64: on W.A (or on B = R^H in G64) with V in
+// W.V. on_b: the matrix
+// is the pivoted QR's B = R^H, Na rows and info[8] columns. with_v: accumulate the right factor V
+// (from V = I when init_v). finalize: write sigma, the normalised left vectors and the order.
+// floor_eps: unit roundoff that sets the noise floor; tol_scale: a pair rotates while
+// |a_i^H a_j| > tol_scale * unit roundoff * |a_i| |a_j| (0: the row count m; < 0: 4 sqrt(m), the
+// resolution of the dot products themselves, for the FP32 sweeps).
 // cnt: [n_work][2] rotation counters; sweeps go to info[sweep_slot].
 template <typename R>
 __global__ void __launch_bounds__(GRID_THREADS)
     k_jacobi_grid(const BondWork* work, int n_work, int max_sweeps, GridSync gs, int* cnt, int* status,
-                  int init_v, int finalize, double floor_eps, int sweep_slot, int on_b) {
+                  int init_v, int finalize, double floor_eps, int sweep_slot, int on_b, int with_v,
+                  double tol_scale) {
   using C2 = typename Cx<R>::T;
   __shared__ int s_Na[MAX_ITEMS];
   __shared__ int s_Ma[MAX_ITEMS];
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(GRID_THREADS)
     s_Ma[w] = Na;
     if (!on_b) s_Ma[w] = Ma;
     s_active[w] = kq >= 2;
-    s_A[w] = on_b ? (C2*)work[w].G64 : Cx<R>::A(work[w]);
+    s_A[w] = on_b ? Cx<R>::B(work[w]) : Cx<R>::A(work[w]);
     s_V[w] = Cx<R>::V(work[w]);
   }
   __syncthreads();
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(GRID_THREADS)
     const int gt = blockIdx.x * blockDim.x + tid, ngt = gridDim.x * blockDim.x;
     for (int w = 0; w < n_work; ++w) {
       const int Na = s_Na[w];
-      if (init_v && !on_b) {
+      if (init_v && with_v) {
         C2* V = s_V[w];
         for (size_t idx = gt; idx < (size_t)Na * Na; idx += ngt) {
           C2 v;
@@ -384,8 +384,9 @@ __global__ void __launch_bounds__(GRID_THREADS)
           else if (sr == 1) { i = i0 + sub; j = j0 + 1 - sub; }
           else { i = sub == 0 ? i0 : j0; j = i + 1; }          // pairs inside each block
           process_pair<R>(s_A[w], s_V[w], work[w].aux, Ma, Na, i, j, s_fro[w], floor_eps, grp, gw, lane, s_part,
-                          s_rot, &cnt[2 * w + par], !on_b, work[w].perm, g_round,
-                          sweep > 0 ? g_round - stride : INT_MIN);
+                          s_rot, &cnt[2 * w + par], with_v != 0, work[w].perm, g_round,
+                          sweep > 0 ? g_round - stride : INT_MIN,
+                          (R)((tol_scale > 0 ? tol_scale : (tol_scale < 0 ? 4.0 * sqrt((double)Ma) : (double)Ma)) * eps));
           named_sync(9 + slot, 32 * GROUP_WARPS * 2);
         }
       }
@@ -404,8 +405,10 @@ __global__ void __launch_bounds__(GRID_THREADS)
     ++sweep;
     if (!grid_barrier(gs, status)) return;
   }
+  // a preconditioning run (no finalize) that reaches its sweep cap is not an error: the FP64 sweeps
+  // that follow finish the job (and report their own non-convergence)
   if (any && blockIdx.x == 0 && tid == 0) {
-    atomicOr(status, ST_SVD_NOCONV);
+    if (finalize) atomicOr(status, ST_SVD_NOCONV);
     for (int w = 0; w < n_work; ++w)
       if (s_active[w]) work[w].info[sweep_slot] = -sweep;
   }
@@ -436,7 +439,10 @@ __global__ void __launch_bounds__(GRID_THREADS)
             __stcg(a + r, x);
           }
         }
-        if (lane == 0 && !(sg == sg)) atomicOr(status, ST_NAN);
+        if (lane == 0 && !(sg == sg)) {
+          atomicOr(status, ST_NAN);
+          atomicOr(work[w].info + 6, FAULT_SIGMA_NAN);
+        }
       }
       base = (base + Na) % ngwarp;
     }
@@ -475,13 +481,13 @@ int jacobi_grid_blocks() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_jacobi_grid<double>, GRID_THREADS, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_jacobi_grid<float>, GRID_THREADS, 0);
-  return (a >= 1 && b >= 1) ? sms : 0;
+  (void)b;
+  return a >= 1 ? sms : 0;
 }
 
 void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3,
-                        int* cnt, int* status, cudaStream_t st, int fp32, int init_v, int finalize,
-                        double floor_eps, int sweep_slot, int on_b) {
+                        int* cnt, int* status, cudaStream_t st, int init_v, int finalize,
+                        double floor_eps, int sweep_slot, int on_b, int with_v, double tol_scale) {
   // the barrier's arrival counter and the abort flag start at zero for every launch
   cudaMemsetAsync(sync3, 0, sizeof(unsigned), st);
   cudaMemsetAsync(sync3 + 2, 0, sizeof(unsigned), st);
@@ -495,12 +501,8 @@ void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sw
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (fp32)
-    cudaLaunchKernelEx(&cfg, k_jacobi_grid<float>, work, n_work, max_sweeps, gs, cnt, status, init_v, finalize,
-                       floor_eps, sweep_slot, 0);
-  else
-    cudaLaunchKernelEx(&cfg, k_jacobi_grid<double>, work, n_work, max_sweeps, gs, cnt, status, init_v, finalize,
-                       floor_eps, sweep_slot, on_b);
+  cudaLaunchKernelEx(&cfg, k_jacobi_grid<double>, work, n_work, max_sweeps, gs, cnt, status, init_v, finalize,
+                     floor_eps, sweep_slot, on_b, with_v, tol_scale);
 }
 
 }  // namespace ptk

@@ -14,6 +14,11 @@ __global__ void k_build_blocks(Tables T, const BondWork* work, int n_work);
 __global__ void k_householder(Tables T, const BondWork* work, int n_work);
 __global__ void k_theta_gate(Tables T, const BondWork* work, int n_work);
 __global__ void k_nan_guard(Tables T, const BondWork* work, int n_work);
+constexpr int BOND_LOG_INTS = 10;
+__global__ void k_bond_log(Tables T, const BondWork* work, int n_work, int layer, int* log, int cap_steps, int nb);
+// the autotuner's synthetic full-capacity state: every Gamma at capacity filled with seeded values
+// in (-1, 1), every lambda with a decaying unit-norm profile (dims set by the host beforehand)
+__global__ void k_tune_fill(Tables T, int n_sites, int n_lams, unsigned seed);
 __global__ void k_truncate(Tables T, const BondWork* work, int n_work, int chi_max, double eps,
                            double mtol);
 __global__ void k_recover(Tables T, const BondWork* work, int n_work);
@@ -29,6 +34,12 @@ __global__ void k_svd_store(const double2* work_A, const double2* work_V, const 
                             const int* perm, int m, int n, int batch, size_t strideA,
                             size_t strideV, double* sigma_out, double2* U, double2* V);
 
+// whole-GPU Householder QR/LQ of the outer blocks of every bond of a layer (hqr_grid.cu)
+int hqr_grid_ok();
+int hqr_grid_fits(int total_cols_cap, int n_items, int blocks);
+void launch_hqr_grid(const Tables& T, const BondWork* work, int n_work, int blocks, unsigned* sync3,
+                     cudaStream_t st);
+
 // cluster-parallel FP64 bond SVD (jacobi_cluster.cu)
 int jacobi_cluster_size(int want);
 void launch_jacobi_cluster(const BondWork* work, int n_work, int cluster, int max_sweeps, int* status,
@@ -37,11 +48,14 @@ void launch_jacobi_cluster(const BondWork* work, int n_work, int cluster, int ma
 // whole-GPU FP64 bond SVD (jacobi_grid.cu): blocks = one per SM (0 if not co-schedulable);
 // sync3: 3 words of device memory (arrival count, unused, abort flag); cnt: 2 ints per item
 int jacobi_grid_blocks();
-// fp32: sweeps in FP32 on A32/V32; init_v: start from V = I; finalize: sigma, U, order;
-// floor_eps: unit roundoff of the noise floor; sweep_slot: info[] index for the sweep count
+// init_v: start from V = I; finalize: sigma, U, order; floor_eps: unit roundoff of the noise floor;
+// sweep_slot: info[] index for the sweep count
+// on_b: B = R^H of the pivoted QR (Na x info[8]); with_v: accumulate V; tol_scale: rotation threshold
+// in units of the unit roundoff (0: the row count)
 void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3,
-                        int* cnt, int* status, cudaStream_t st, int fp32 = 0, int init_v = 1, int finalize = 1,
-                        double floor_eps = 1.1102230246251565e-16, int sweep_slot = 3, int on_b = 0);
+                        int* cnt, int* status, cudaStream_t st, int init_v = 1, int finalize = 1,
+                        double floor_eps = 1.1102230246251565e-16, int sweep_slot = 3, int on_b = 0,
+                        int with_v = 1, double tol_scale = 0.0);
 
 // QR preconditioning of the bond SVD (qrcp.cu): pivoted QR of D into Y64, B = R^H into G64;
 // after the Jacobi on B: V_D = P U', U_D = D V_D / sigma
@@ -50,20 +64,16 @@ int qrcp_smem_cluster(int m_cap, int n_cap);
 // whole-GPU variant (cooperative, one CTA per SM): usable when qrcp_grid_ok() and the layer fits
 int qrcp_grid_ok();
 int qrcp_grid_fits(int n_work, int m_cap, int total_cols_cap, int blocks);
-void launch_qrcp_grid(const BondWork* work, int n_work, int blocks, unsigned* sync3, int* status, cudaStream_t st);
+// tau2: squared relative noise level of D at which the pivoted QR stops (rank-revealing);
+// kmax: stop after at most kmax reflectors (the autotuner times a prefix; otherwise INT_MAX)
+void launch_qrcp_grid(const BondWork* work, int n_work, int blocks, unsigned* sync3, double tau2, int kmax,
+                      int* status, cudaStream_t st);
 void launch_qrcp_precondition(const BondWork* work, int n_work, int cluster, int smem_cluster, int k_cap, int m_cap,
-                              int* status, cudaStream_t st);
-void launch_qrcp_finish(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st);
-void launch_mix_gemm_av(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st,
-                        bool rank_cols = false);
-
-// optional fast-path SVD on D (PT_TEBD_SVD=mixed): FP32 bulk sweeps + FP64 Newton-Schulz
-// re-orthonormalisation + FP64 polish (mixed_svd.cu)
-void launch_mixed_fp32(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,
-                       int* status, cudaStream_t st);
-void launch_mixed_reorth(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st);
-void launch_mixed_fp64(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3, int* cnt,
-                       int* status, double polish_floor, cudaStream_t st);
+                              double tau2, int kmax, int* status, cudaStream_t st);
+// after the truncation: V_D and U_D on the kept columns (lam_chi: the tables' bond dims)
+void launch_qrcp_finish(const BondWork* work, int n_work, int k_cap, int m_cap, const int* lam_chi,
+                        cudaStream_t st);
+void launch_mix_gemm_av(const BondWork* work, int n_work, int k_cap, int m_cap, const int* lam_chi, cudaStream_t st);
 
 // tensor-core theta + gate of the fast path (tc_theta.cu); precision: 1 TF32x3, 2 BF16x3, 3 TF32x1,
 // 4 BF16 fixed-point slices. Packed operand bytes of a bond (which: 0 = A, 1 = B'), its output tile

@@ -86,36 +86,6 @@ __global__ void k_site_swap(Tables T, const SiteWork* work, int n_work) {
   T.site_kappa[s] = T.mpo_kappa[T.mpo_kappa_off[m] + k + 1];
 }
 
-// ------------------------------------------------------------------ bond dims helper
-struct BondDims {
-  int sL, sR, BL, BC, BR;
-  int chl, chc, chr, kL, kR;
-  int mL, nL, mR, nR;
-  bool qrL, lqR;
-  int rL, rR, mD, nD;
-};
-
-PT_DEV BondDims bond_dims(const Tables& T, const BondWork& W) {
-  BondDims d;
-  d.sL = W.site_l; d.sR = W.site_l + 1;
-  d.BL = W.lam_l; d.BC = W.lam_l + 1; d.BR = W.lam_l + 2;
-  d.chl = T.lam_chi[d.BL]; d.chc = T.lam_chi[d.BC]; d.chr = T.lam_chi[d.BR];
-  d.kL = T.site_kappa[d.sL]; d.kR = T.site_kappa[d.sR];
-  d.mL = d.chl * d.kL; d.nL = 4 * d.chc;
-  d.mR = 4 * d.chc; d.nR = d.kR * d.chr;
-  d.qrL = d.mL > d.nL;
-  d.lqR = d.nR > d.mR;
-  d.rL = d.qrL ? d.nL : d.mL;
-  d.rR = d.lqR ? d.mR : d.nR;
-  d.mD = 4 * d.rL; d.nD = 4 * d.rR;
-  return d;
-}
-
-PT_DEV bool bond_fits(const BondDims& d, const BondWork& W) {
-  return d.mL <= W.mL_cap && d.nL <= W.nL_cap && d.mR <= W.mR_cap && d.nR <= W.nR_cap &&
-         d.mD <= W.mD_cap && d.nD <= W.nD_cap;
-}
-
 // ------------------------------------------------------------------ K2a: B_L and B_R^H
 // App. A.2 (c-d): B_L = lambda_{n-1} Gamma_n as [(l,a),(p,c)], B_R = Gamma_{n+1} lambda_{n+1} as
 // [(c,q),(b,r)]. B_L is stored column-major in QL; B_R^H column-major in QR.
@@ -124,6 +94,7 @@ __global__ void k_build_blocks(Tables T, const BondWork* work, int n_work) {
   if (w >= n_work) return;
   const BondWork& W = work[w];
   const BondDims d = bond_dims(T, W);
+  if (blockIdx.x == 0 && threadIdx.x == 0) W.info[6] = 0;   // this update's fault flags
   if (!bond_fits(d, W)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(T.status, ST_CAPACITY);
     return;
@@ -321,6 +292,7 @@ __global__ void k_nan_guard(Tables T, const BondWork* work, int n_work) {
     W.info[0] = 0;
     W.info[1] = 0;
     W.info[7] = 0;
+    W.info[6] |= FAULT_D_NONFINITE;
     atomicOr(T.status, ST_NAN);
   }
 }
@@ -383,9 +355,67 @@ __global__ void k_truncate(Tables T, const BondWork* work, int n_work, int chi_m
     T.lam_lognorm[BC] += log(nrm);
   } else {
     atomicOr(T.status, ST_NAN);
+    W.info[6] |= FAULT_ZERO_NORM;
     for (int i = 0; i < chi; ++i) lam[i] = 0.0;
   }
   T.lam_chi[BC] = chi;
+  // discarded weight ||sigma_{>= chi}||_2 / sigma_max of this update, for the bond log
+  double tail2 = 0.0;
+  for (int i = chi; i < n; ++i) tail2 += W.sig[W.perm[i]] * W.sig[W.perm[i]];
+  const double smax = W.sig[W.perm[0]];
+  *(double*)(W.info + 10) = smax > 0.0 ? sqrt(tail2) / smax : 0.0;
+}
+
+// ------------------------------------------------------------------ bond log
+// One record per bond update (one thread per bond of the layer): D's shape, the pivoted QR's rank,
+// the Jacobi sweeps, the update's fault flags (FAULT_*), the new bond dimension, the two sites'
+// augmented dimensions, and the discarded weight (two ints holding a double). log: [steps][6 layers][nb][BOND_LOG_INTS].
+__global__ void k_bond_log(Tables T, const BondWork* work, int n_work, int layer, int* log, int cap_steps,
+                           int nb) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n_work) return;
+  const int k = *T.step;
+  if (k >= cap_steps) return;
+  const BondWork& W = work[w];
+  int* r = log + (((size_t)k * 6 + layer) * nb + w) * BOND_LOG_INTS;
+  r[0] = W.info[0];
+  r[1] = W.info[1];
+  r[2] = W.info[8];
+  r[3] = W.info[3];
+  r[4] = W.info[6];
+  r[5] = T.lam_chi[W.lam_l + 1];
+  r[6] = T.site_kappa[W.site_l];
+  r[7] = T.site_kappa[W.site_l + 1];
+  r[8] = W.info[10];
+  r[9] = W.info[11];
+}
+
+// ------------------------------------------------------------------ autotuner's synthetic state
+// A counter-based hash (a 64-bit finaliser) gives every entry a value in (-1, 1): no state, the same
+// values for the same (seed, site, index) on every launch.
+PT_DEV double hash_unit(unsigned long long x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdULL;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ULL;
+  x ^= x >> 33;
+  return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+__global__ void k_tune_fill(Tables T, int n_sites, int n_lams, unsigned seed) {
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
+  for (int s = 0; s < n_sites; ++s) {
+    double2* G = T.site_gam[s];
+    const unsigned long long base = ((unsigned long long)seed << 40) ^ ((unsigned long long)s << 28);
+    for (size_t i = tid; i < T.site_cap[s]; i += nt)
+      G[i] = make_double2(hash_unit(base + 2 * i), hash_unit(base + 2 * i + 1));
+  }
+  for (int B = 0; B < n_lams; ++B) {
+    const int chi = T.lam_chi[B];
+    double nrm2 = 0.0;
+    for (int i = 0; i < chi; ++i) nrm2 += exp(-i / 4.0);          // sum of the squares below
+    for (size_t i = tid; i < (size_t)chi; i += nt) T.lam_ptr[B][i] = exp(-(double)i / 8.0) / sqrt(nrm2);
+  }
 }
 
 // ------------------------------------------------------------------ K6: Gamma recovery

@@ -8,10 +8,10 @@
 //      matrix with the columns in shared memory or, for large matrices, in global memory
 //      (k_qrcp_cl);
 //   2. the grid Jacobi on B gives B = U' S V'^H, i.e. R = V' S U'^H and D = (Q V') S (P U')^H;
-//   3. k_qrcp_vd: V_D = P U' (rows permuted back);
-//   4. U_D = D V_D S^{-1} by an FP64 GEMM (k_mix_gemm op 2) and a column scaling (k_qrcp_ud). Its
-//      error in column c is ~eps ||D|| / s_c, and that column enters the truncated state scaled by
-//      s_c, so the state error stays at rounding level; Q is never formed.
+//   3. after the truncation, k_qrcp_vd: V_D = P U' (rows permuted back) on the kept columns;
+//   4. U_D = D V_D S^{-1} on the kept columns by an FP64 GEMM (k_mix_gemm) and a column scaling
+//      (k_qrcp_ud). Its error in column c is ~eps ||D|| / s_c, and that column enters the truncated
+//      state scaled by s_c, so the state error stays at rounding level; Q is never formed.
 #include <cooperative_groups.h>
 
 #include "grid_sync.cuh"
@@ -63,17 +63,20 @@ constexpr int QR_SMEM_THREADS = 512;
 // where that cancels below sqrt(eps) of the last exact value (the safeguard of LAPACK's pivoted
 // QR); they only choose pivots. The reflector uses the exact norm of the pivot column.
 // Rank-revealing stop: the factorisation ends at the first step j whose pivot column (the largest
-// remaining one) has an exact norm^2 <= u^2 ||D||_F^2 (u = 2^-53): every remaining column is then
-// at the FP64 noise floor (the level below which the Jacobi does not rotate a column either), and
-// the trailing block R22 they form, ||R22||_F <= sqrt(n) u ||D||_F, is dropped -- a perturbation
-// within the backward error of any FP64 SVD. R is then k x n (k = j, recorded in info[8]) and
+// remaining one) has an exact norm^2 <= tau^2 ||D||_F^2, with tau the noise level of D: u = 2^-53
+// when D was formed in FP64 (the level below which the Jacobi does not rotate a column either),
+// 2^-40 for the fixed-point-slice tensor-core product (whose error in D's null space is ~3e-14 of
+// ||D||_F). Every remaining column is then noise, and the trailing block R22 they form,
+// ||R22||_F <= sqrt(n) tau ||D||_F, is dropped -- for tau = u a perturbation within the backward
+// error of any FP64 SVD, for 2^-40 one far below every truncation threshold (>= 1e-10 sigma_1). R is then k x n (k = j, recorded in info[8]) and
 // B = R^H is n x k, so the Jacobi runs on k columns. (The workloads' D are often exactly rank
 // deficient: a conserved magnetisation leaves ~n/4 nonzero singular values.)
 // Dynamic shared memory: [X[lq_cap][m_cap] if !GL] | hv[m_cap] | beta[lq_cap] (double2),
 // nrm[lq_cap] | nref[lq_cap] (double), qp[n_cap] | pos[n_cap] | done[lq_cap] (int).
 template <bool GL>
 __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
-    k_qrcp_cl(const BondWork* work, int n_work, int lq_cap, int m_cap, int n_cap, int* status) {
+    k_qrcp_cl(const BondWork* work, int n_work, int lq_cap, int m_cap, int n_cap, double tau2, int kmax,
+              int* status) {
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int w = blockIdx.x / C;
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
     // ||D||_F^2 from the C shares, summed in the same order in every CTA
     double f = 0;
     for (int r = 0; r < C; ++r) f += *cl.map_shared_rank(&s_fro, r);
-    s_thr2 = 1.232595164407831e-32 * f;            // (2^-53)^2 ||D||_F^2
+    s_thr2 = tau2 * f;                             // tau^2 ||D||_F^2
   }
   for (int j = 0; j < Na; ++j) {
     const int par = j & 1;
@@ -213,8 +216,9 @@ __global__ void __launch_bounds__(QR_SMEM_THREADS, 1)
       // v^H v = 2 ||x|| (||x|| + |alpha|), so kappa = 1 / (||x|| (||x|| + |alpha|))
       double nrm2 = 0;
       for (int k = 0; k < nw; ++k) nrm2 += s_red[k];
-      if (nrm2 <= s_thr2) {
-        // every remaining column is at the noise floor: stop (same decision in every CTA)
+      if (nrm2 <= s_thr2 || j >= kmax) {
+        // every remaining column is at the noise floor (or the caller's step limit): stop, the same
+        // decision in every CTA
         s_stop = 1;
         s_k = j;
       } else {
@@ -344,7 +348,7 @@ constexpr int QRG_RC = 8;                 // rows per lane held in registers: Ma
 // The same rank-revealing stop as k_qrcp_cl ends a matrix at the first pivot at the noise floor.
 // Finally every warp writes the row of B = R^H (Na x k) that belongs to its column.
 __global__ void __launch_bounds__(QRG_THREADS, 1)
-    k_qrcp_grid(const BondWork* work, int n_work, GridSync gs, int* status) {
+    k_qrcp_grid(const BondWork* work, int n_work, GridSync gs, double tau2, int kmax, int* status) {
   extern __shared__ double2 hv[];
   __shared__ int s_off[QRG_MAX_ITEMS + 1];
   __shared__ int s_Ma[QRG_MAX_ITEMS];
@@ -439,7 +443,7 @@ __global__ void __launch_bounds__(QRG_THREADS, 1)
     for (int i = lane; i < Na; i += 32) f += __ldcg(work[w].aux + i);
     f = wsum(f);
     if (lane == 0) {
-      s_thr2[w] = 1.232595164407831e-32 * f;   // (2^-53)^2 ||D||_F^2
+      s_thr2[w] = tau2 * f;                     // tau^2 ||D||_F^2
       s_kst[w] = Na;
     }
   }
@@ -495,8 +499,9 @@ __global__ void __launch_bounds__(QRG_THREADS, 1)
         double nrm2 = 0;
         for (int k = 0; k < QRG_WARPS; ++k) nrm2 += s_red[k];
         s_stopnow = 0;
-        if (nrm2 <= s_thr2[w]) {
-          // every remaining column is at the noise floor: this matrix stops at rank j
+        if (nrm2 <= s_thr2[w] || j >= kmax) {
+          // every remaining column is at the noise floor (or the caller's step limit): this matrix
+          // stops at rank j
           s_stopnow = 1;
           s_kst[w] = j;
         } else {
@@ -629,34 +634,38 @@ __global__ void __launch_bounds__(QRG_THREADS, 1)
   }
 }
 
-// V_D = P U': V[qperm[k], c] = U'[k, c] (U' = the normalised columns of B after the Jacobi)
-__global__ void k_qrcp_vd(const BondWork* work, int n_work) {
+// The finish forms only the columns the truncation keeps (it runs after k_truncate): kept column c
+// is Jacobi column perm[c], c < chi = the bond's new dimension.
+// V_D = P U' on the kept columns: V[qperm[r], perm[c]] = U'[r, perm[c]] (U' = the normalised columns
+// of B after the Jacobi)
+__global__ void k_qrcp_vd(const BondWork* work, int n_work, const int* lam_chi) {
   const int w = blockIdx.y;
   if (w >= n_work) return;
   const BondWork& W = work[w];
   int Ma, Na;
   shape(W, &Ma, &Na);
-  const int kq = min(W.info[8], Na);              // the pivoted QR's rank
-  const size_t tot = (size_t)Na * kq;
+  const int kept = min(lam_chi[W.lam_l + 1], Na);
+  const size_t tot = (size_t)Na * kept;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(idx % Na), c = (int)(idx / Na);
-    W.V[W.qperm[k] + (size_t)c * Na] = W.G64[idx];
+    const int r = (int)(idx % Na), col = W.perm[idx / Na];
+    W.V[W.qperm[r] + (size_t)col * Na] = W.G64[r + (size_t)col * Na];
   }
 }
 
-// U_D = (D V_D) / sigma, column by column (Y64 holds D V_D)
-__global__ void k_qrcp_ud(const BondWork* work, int n_work) {
+// U_D = (D V_D) / sigma on the kept columns (Y64 holds D V_D in kept order)
+__global__ void k_qrcp_ud(const BondWork* work, int n_work, const int* lam_chi) {
   const int w = blockIdx.y;
   if (w >= n_work) return;
   const BondWork& W = work[w];
   int Ma, Na;
   shape(W, &Ma, &Na);
-  const size_t tot = (size_t)Ma * min(W.info[8], Na);   // the k columns with a singular value
+  const int kept = min(lam_chi[W.lam_l + 1], Na);
+  const size_t tot = (size_t)Ma * kept;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(idx / Ma);
-    const double s = W.sig[c];
+    const int col = W.perm[idx / Ma];
+    const double s = W.sig[col];
     const double2 y = W.Y64[idx];
-    W.A[idx] = s > 0.0 ? make_double2(y.x / s, y.y / s) : make_double2(0.0, 0.0);
+    W.A[idx % Ma + (size_t)col * Ma] = s > 0.0 ? make_double2(y.x / s, y.y / s) : make_double2(0.0, 0.0);
   }
 }
 
@@ -725,7 +734,8 @@ int qrcp_grid_fits(int n_work, int m_cap, int total_cols_cap, int blocks) {
          (total_cols_cap + blocks - 1) / blocks <= QRG_WARPS;
 }
 
-void launch_qrcp_grid(const BondWork* work, int n_work, int blocks, unsigned* sync3, int* status, cudaStream_t st) {
+void launch_qrcp_grid(const BondWork* work, int n_work, int blocks, unsigned* sync3, double tau2, int kmax,
+                      int* status, cudaStream_t st) {
   cudaMemsetAsync(sync3, 0, sizeof(unsigned), st);
   cudaMemsetAsync(sync3 + 2, 0, sizeof(unsigned), st);
   GridSync gs{sync3, (int*)(sync3 + 2), GRID_WAIT_LIMIT_CYCLES};
@@ -739,7 +749,7 @@ void launch_qrcp_grid(const BondWork* work, int n_work, int blocks, unsigned* sy
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_qrcp_grid, work, n_work, gs, status);
+  cudaLaunchKernelEx(&cfg, k_qrcp_grid, work, n_work, gs, tau2, kmax, status);
 }
 
 // Cluster size for the global-memory variant (at most `want` CTAs per matrix; 1 at the least).
@@ -749,21 +759,22 @@ int qrcp_cluster_size(int want, int m_cap, int n_cap) {
 }
 
 void launch_qrcp_precondition(const BondWork* work, int n_work, int cluster, int smem_cluster, int k_cap, int m_cap,
-                              int* status, cudaStream_t st) {
+                              double tau2, int kmax, int* status, cudaStream_t st) {
   cudaLaunchAttribute at[1];
   const bool gl = smem_cluster <= 0;
   const int c = gl ? cluster : smem_cluster;
   const int lq = (k_cap + c - 1) / c;
   cudaLaunchConfig_t cfg = qr_cfg(n_work, c, st, at);
   cfg.dynamicSmemBytes = qr_smem_bytes(lq, m_cap, k_cap, gl);
-  if (gl) cudaLaunchKernelEx(&cfg, k_qrcp_cl<true>, work, n_work, lq, m_cap, k_cap, status);
-  else cudaLaunchKernelEx(&cfg, k_qrcp_cl<false>, work, n_work, lq, m_cap, k_cap, status);
+  if (gl) cudaLaunchKernelEx(&cfg, k_qrcp_cl<true>, work, n_work, lq, m_cap, k_cap, tau2, kmax, status);
+  else cudaLaunchKernelEx(&cfg, k_qrcp_cl<false>, work, n_work, lq, m_cap, k_cap, tau2, kmax, status);
 }
 
-void launch_qrcp_finish(const BondWork* work, int n_work, int k_cap, int m_cap, cudaStream_t st) {
-  k_qrcp_vd<<<dim3(128, n_work), 256, 0, st>>>(work, n_work);
-  launch_mix_gemm_av(work, n_work, k_cap, m_cap, st, /*rank_cols=*/true);
-  k_qrcp_ud<<<dim3(128, n_work), 256, 0, st>>>(work, n_work);
+void launch_qrcp_finish(const BondWork* work, int n_work, int k_cap, int m_cap, const int* lam_chi,
+                        cudaStream_t st) {
+  k_qrcp_vd<<<dim3(128, n_work), 256, 0, st>>>(work, n_work, lam_chi);
+  launch_mix_gemm_av(work, n_work, k_cap, m_cap, lam_chi, st);
+  k_qrcp_ud<<<dim3(128, n_work), 256, 0, st>>>(work, n_work, lam_chi);
 }
 
 }  // namespace ptk

@@ -14,15 +14,18 @@
 //     rounding of the remainder;
 //   * fixed-point slices (PT_BF16_OZAKI; Ozaki, Ogita, Oishi and Rump's error-free splitting of
 //     matrix products): the row is scaled by a power of two 2^-e_row so every entry lies in (-1, 1),
-//     then cut into NS = 5 slices a_i 2^(-b(i+1)) with integer a_i, |a_i| <= 2^b (b = 7 while
+//     then cut into NS = 6 slices a_i 2^(-b(i+1)) with integer a_i, |a_i| <= 2^b (b = 7 while
 //     K <= 512). A product of two slices is exact in FP32 and the sum over K of the level-0 (and
 //     level-1) slice products is an integer multiple of one power of two below 2^24, so the tensor
-//     cores' FP32 accumulation of those levels is exact; the higher levels carry only their own
-//     rounding, ~2^-24 of a quantity 2^-2b smaller. The product is accurate to ~1e-9 relative to
-//     the rows' scale (FP32 accumulation of unscaled pieces gives ~1e-6 there).
+//     cores' FP32 accumulation of those levels is exact; level 2 and the levels beyond carry only
+//     their own rounding, ~2^-24 of quantities 2^-2b and 2^-3b smaller. The product is accurate to
+//     ~1e-12 relative to the rows' scale (FP32 accumulation of unscaled pieces gives ~1e-6 there),
+//     which also keeps the exact null space of a rank-deficient D at that level, below the
+//     rank-revealing stop of the pivoted QR that follows.
 // Complex products take four real products (Re = Ar Br - Ai Bi with the MMA's negate-A bit,
-// Im = Ar Bi + Ai Br). The piece products accumulate in three TMEM accumulator pairs by level
-// (i + j = 0, 1, >= 2); the epilogue adds them in FP64 and applies 2^(e_row(A) + e_row(B')).
+// Im = Ar Bi + Ai Br). The piece products accumulate in TMEM accumulator pairs by level
+// (i + j = 0, 1, 2, >= 3; two levels 0, 1-2 for three pieces); the epilogue adds them in FP64 and
+// applies 2^(e_row(A) + e_row(B')).
 //
 // Data flow. Pack kernels write each operand's 2 NS planes (real/imaginary x pieces) in the tcgen05
 // canonical K-major no-swizzle layout (8-row x 16-byte core matrices), one block per plane, row tile
@@ -47,7 +50,8 @@ namespace {
 constexpr int TMA = 128;            // A tile rows (u)
 constexpr int TNB = 64;             // B' tile rows (n') = output tile columns
 constexpr int TC_THREADS = 128;
-constexpr int STAGES = 3;
+constexpr int MAX_STAGES = 3;     // shared-memory stages of the K pipeline (2 for six slices: 227 KB)
+template <int NS> struct Stages { static constexpr int value = NS >= 6 ? 2 : MAX_STAGES; };
 constexpr int MAX_ITEMS = 1024;
 constexpr uint32_t ROW_BYTES = 32;  // one K step of one row: 8 tf32 or 16 bf16 (two 16-byte K groups)
 constexpr long long SPIN_LIMIT = 20000000;  // mbarrier polls before giving up
@@ -397,8 +401,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_theta(Tables T, const Bond
   using G = Geo<BF16>;
   constexpr uint32_t A_PLANE = TMA * ROW_BYTES, B_PLANE = TNB * ROW_BYTES;
   constexpr uint32_t A_STAGE = 2 * NS * A_PLANE, B_STAGE = 2 * NS * B_PLANE, STAGE = A_STAGE + B_STAGE;
+  constexpr int STAGES = Stages<NS>::value;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ uint64_t bar_full[STAGES], bar_empty[STAGES];
+  __shared__ uint64_t bar_full[MAX_STAGES], bar_empty[MAX_STAGES];
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
   __shared__ int col_exp[TNB];
@@ -447,11 +452,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_theta(Tables T, const Bond
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_s;
-  // accumulator pairs by level L (i + j = 0, 1, >= 2): columns [2 L TNB, (2 L + 1) TNB) hold the
-  // real part, the next TNB columns the imaginary part
+  // accumulator pairs by level L = min(i + j, NLEV - 1): columns [2 L TNB, (2 L + 1) TNB) hold the
+  // real part, the next TNB columns the imaginary part (4 levels x 2 x 64 columns = all of TMEM)
   const uint32_t idesc = instr_desc(BF16 ? 1u : 2u, TMA, TNB);
   constexpr uint32_t LBO_A = TMA * 16, LBO_B = TNB * 16, SBO = 128;
-  constexpr int NLEV = NS == 1 ? 1 : 3;
+  constexpr int NLEV = NS == 1 ? 1 : (NS <= 3 ? 3 : 4);
   uint32_t g = 0;                 // K steps processed by this CTA (stage = g % STAGES)
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     int lo = 0, hi = n_work - 1;
@@ -482,7 +487,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_theta(Tables T, const Bond
       bool ok = true;
       uint32_t loaded = g, waited = g, committed = 0;
       bool any_commit = false;
-      bool init[3] = {false, false, false};
+      bool init[4] = {false, false, false, false};
       // prologue: the first STAGES - 1 steps (their stages were freed by the previous tile's end)
       for (int ks = 0; ks < n_ks && ks < STAGES - 1; ++ks) {
         load(ks, g + ks);
@@ -500,7 +505,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_theta(Tables T, const Bond
         for (int i = 0; i < NS; ++i) {
 #pragma unroll
           for (int j = 0; j < NS - i; ++j) {
-            const int L = (i + j) < 2 ? (i + j) : 2;
+            const int L = (i + j) < NLEV - 1 ? (i + j) : NLEV - 1;
             const uint32_t dre = tmem + (2 * L) * TNB, dim = dre + TNB;
             const uint64_t ar = smem_desc(sa + i * A_PLANE, LBO_A, SBO);
             const uint64_t ai = smem_desc(sa + (NS + i) * A_PLANE, LBO_A, SBO);
@@ -603,7 +608,7 @@ Mode mode_of(int precision) {
     case 1: return {false, 3};   // TF32x3: natural split
     case 2: return {true, 3};    // BF16x3: natural split
     case 3: return {false, 1};   // TF32x1
-    default: return {true, 5};   // BF16 fixed-point slices (Ozaki)
+    default: return {true, 6};   // BF16 fixed-point slices (Ozaki)
   }
 }
 
@@ -620,7 +625,7 @@ void launch_mode(const Tables& T, const BondWork* work, int n_work, int tile_cap
   }
   k_tc_pack<BF16, NS, SLICE><<<dim3(gx, n_work), 256, 0, st>>>(T, work, n_work, 0);
   k_tc_pack<BF16, NS, SLICE><<<dim3(4 * gx, n_work), 256, 0, st>>>(T, work, n_work, 1);
-  const size_t smem = (size_t)STAGES * 2 * NS * (TMA + TNB) * ROW_BYTES + 1024;
+  const size_t smem = (size_t)Stages<NS>::value * 2 * NS * (TMA + TNB) * ROW_BYTES + 1024;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -652,7 +657,7 @@ void launch_tc_theta(const Tables& T, const BondWork* work, int n_work, int tile
     case 1: launch_mode<false, 3, false>(T, work, n_work, tile_cap, precision, st); break;
     case 2: launch_mode<true, 3, false>(T, work, n_work, tile_cap, precision, st); break;
     case 3: launch_mode<false, 1, false>(T, work, n_work, tile_cap, precision, st); break;
-    default: launch_mode<true, 5, true>(T, work, n_work, tile_cap, 4, st); break;
+    default: launch_mode<true, 6, true>(T, work, n_work, tile_cap, 4, st); break;
   }
 }
 

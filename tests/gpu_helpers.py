@@ -29,12 +29,12 @@ def engine_args_from_oracle(cis):
     return chains, mpos
 
 
-def run_gpu(w, cis, ops, K=None, precision="fp64", insert=None, use_graph=True, multiplet_tol=1e-12):
+def run_gpu(w, cis, ops, K=None, precision="fp64", insert=None, use_graph=True, multiplet_tol=1e-12, route=None):
     import paper_2201_05529_gb300._capi as capi
     K = w.K if K is None else K
     chains, mpos = engine_args_from_oracle(cis)
     eng = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, precision=precision,
-                      multiplet_tol=multiplet_tol, max_steps=K, use_graph=use_graph)
+                      multiplet_tol=multiplet_tol, max_steps=K, use_graph=use_graph, route=route)
     if insert is not None:
         c, n, A, side = insert
         eng.apply_local(c, n, A, side)

@@ -69,4 +69,4 @@ def test_reference_arm_prints_one_complete_json_line():
         assert key in d, key
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
-    assert d["config"]["workload"] == "xyz5_twobaths"
+    assert d["config"]["workload"] == "xy21_allbaths"

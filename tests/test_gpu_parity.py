@@ -206,22 +206,45 @@ def test_standalone_svd_against_lapack():
             assert np.max(np.abs(U[i].conj().T @ U[i] - np.eye(k))) < 1e-12 * max(m, n)
 
 
-@pytest.mark.parametrize("env", [{"PT_TEBD_QR": "cluster"}, {"PT_TEBD_QR": "global"},
-                                 {"PT_TEBD_PRECOND": "0"}, {"PT_TEBD_SVD": "mixed"}])
-def test_alternative_svd_routes(env, monkeypatch):
-    # every selectable bond-SVD route (pivoted QR in cluster shared memory or in global memory,
-    # the Jacobi on D without preconditioning, the mixed FP32/FP64 sweeps of the fast path) is
-    # held to the same bar as the default on an uncapped window (the engine reads them at init)
-    for k, v in env.items():
-        monkeypatch.setenv(k, v)
-    w = workload("xyz5_twobaths", K=12, chi_max=256)
+@pytest.mark.parametrize("route", [("grid", "grid"), ("cluster_smem", "grid"), ("cluster_global", "grid"),
+                                   ("grid", "cta"), ("cluster_global", "cta")])
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("bf16_ozaki", 1e-5)])
+def test_every_route_the_tuner_can_pick(route, precision, tol):
+    # every candidate of the autotuner (pivoted QR of the SVD on the whole GPU, in cluster shared
+    # memory, in cluster global memory; outer-block QR on the whole GPU or one CTA per block) forced
+    # on a twelve-step window of the five-site chain (chi_max 64: every route fits), against the oracle
+    import paper_2201_05529_gb300._capi as capi
+    w = workload("xyz5_twobaths", K=12, chi_max=64)
     cis = oprob.build_inputs(w)
-    if "PT_TEBD_SVD" in env:
-        # a fast-path route (bf16_ozaki theta + gate): the fast path's strict 1e-5 on this
-        # uncapped window
-        _, obs, _ = run_gpu(w, cis, OPS, precision="bf16_ozaki")
-        ref = run_oracle(w, cis, OPS)[0]
-        err = np.abs(obs[:, 0, :5, :] - ref.obs).max(axis=(1, 2))
-        assert np.max(err) < 1e-5, err
-    else:
-        _compare(w, cis)
+    try:
+        eng, obs, tr = run_gpu(w, cis, OPS, precision=precision, route=route)
+    except capi.PTError as ex:
+        # a route this device cannot co-schedule (cluster shared memory needs 16-CTA clusters)
+        assert ex.code == -1 and "does not fit" in str(ex) and route[0] == "cluster_smem", ex
+        pytest.skip(f"route {route} does not fit on this device")
+    r = eng.routes()
+    assert r["odd"][:2] == route and r["even"][:2] == route
+    ref = run_oracle(w, cis, OPS)[0]
+    err = np.abs(obs[:, 0, :5, :] - ref.obs).max(axis=(1, 2))
+    assert np.max(err) < tol, err
+    eng.destroy()
+
+
+def test_tuner_times_once_then_reads_its_cache(tmp_path):
+    import paper_2201_05529_gb300._capi as capi
+    from tests.gpu_helpers import engine_args_from_oracle
+    w = workload("xyz5_twobaths", K=4)
+    chains, mpos = engine_args_from_oracle(oprob.build_inputs(w))
+    cache = str(tmp_path / "tune.tsv")
+    e1 = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, max_steps=w.K, autotune=True, tune_cache=cache)
+    r1 = e1.routes()
+    assert r1["odd"][2] and not r1["odd"][3]                  # timed, not from the cache
+    assert min(t for t in r1["odd"][4] if t >= 0) > 0
+    e1.step(4)
+    e1.sync()
+    e1.destroy()
+    e2 = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, max_steps=w.K, autotune=True, tune_cache=cache)
+    r2 = e2.routes()
+    assert r2["odd"][3] and r2["odd"][:2] == r1["odd"][:2] and r2["even"][:2] == r1["even"][:2]
+    e2.destroy()
+    assert len(open(cache).read().splitlines()) == 2           # one line per layer shape

@@ -109,3 +109,63 @@ def test_random_stress_state_singular_values():
     print(f"random stress N=8: max |lambda - oracle| = {worst:.2e}")
     assert worst < 1e-9
     eng.destroy()
+
+
+@pytest.fixture(scope="module")
+def xy21_ten_steps():
+    # the 21-site workload itself, first 10 steps (chi reaches ~85, D up to ~1300 x 1300): the oracle
+    # with its own PT-MPOs (tens of seconds on the host cores)
+    w = workload("xy21_allbaths", K=10)
+    cis = oprob.build_inputs(w)
+    return w, cis, run_oracle(w, cis, OPS)[0]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("bf16_ozaki", 1e-5)])
+def test_xy21_first_ten_steps_parity(xy21_ten_steps, precision, tol):
+    w, cis, ref = xy21_ten_steps
+    eng, obs, tr = run_gpu(w, cis, OPS, precision=precision)
+    err = np.abs(obs[:, 0, :21, :] - ref.obs).max(axis=(1, 2))
+    print(f"xy21 {precision}: max |obs - oracle| per step {np.array2string(err, precision=2)}")
+    assert np.max(err) < tol
+    assert np.max(np.abs(tr[:, 0] - ref.trace)) < tol
+    chi, kap = eng.get_dims(0)
+    if precision == "fp64":
+        assert list(chi) == list(ref.chis[-1]) and list(kap) == list(ref.kappas[-1])
+    # the bond blocks went through the large-matrix routes: D above 256 (cluster pivoted QR) and a
+    # rank-revealing stop well below D's size
+    log, _ = eng.read_bond_log(0, w.K)
+    mD, nD, k = log[..., 0], log[..., 1], log[..., 2]
+    big = np.minimum(mD, nD) > 256
+    assert np.any(big)
+    assert np.all(k[big] < np.minimum(mD, nD)[big])
+    eng.destroy()
+
+
+def test_tuning_at_capacity_leaves_the_state_untouched():
+    # the autotuner runs every candidate on a synthetic state at full capacity (the outer-block QR's
+    # reflector scalars fill 4 chi_c entries of a bond's scratch, more than its SVD needs on the
+    # chain's edge bonds), then restores the initial state: the tuned engine must reproduce, bit for
+    # bit, an untuned engine forced onto the same routes
+    import paper_2201_05529_gb300._capi as capi
+    from paper_2201_05529_gb300 import problem as pp
+    w = workload("xy21_allbaths", K=4)
+    chains, mpos = pp.build_problem(w)
+    runs = []
+    for kw in (dict(autotune=True, tune_cache=None), None):
+        if kw is None:
+            r = runs[0][1]
+            kw = dict(autotune=False, route=r["odd"][:2]) if r["odd"][:2] == r["even"][:2] else None
+            if kw is None:
+                pytest.skip("the tuner chose different routes for the two layers")
+        e = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, max_steps=w.K, **kw)
+        e.set_observables(OPS)
+        routes = e.routes()
+        e.step(w.K)
+        e.sync()
+        obs, tr = e.read_history(0, w.K + 1)
+        flags = e.get_svd_sweeps()[:, 1]
+        e.destroy()
+        assert np.all(flags == 0)
+        runs.append(((obs, tr), routes))
+    assert runs[0][1]["odd"][2] and not runs[1][1]["odd"][2]         # tuned, then forced
+    assert np.array_equal(runs[0][0][0], runs[1][0][0]) and np.array_equal(runs[0][0][1], runs[1][0][1])
