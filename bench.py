@@ -419,49 +419,69 @@ def run_ours(args, rank, world, local):
     if not args.no_secondary and args.workload != SECONDARY_WORKLOAD:
         out["secondary"] = _secondary(capi, pp, workload, torch, stream, flush, args.precision)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, W, K)
     if world > 1:
         dist.destroy_process_group()
     return out
 
 
 # ------------------------------------------------------------------------ the oracle on the host
-def _oracle_steps(w, seconds, max_steps):
-    """The FP64 oracle as it stands from t = 0: steps timed one by one until `seconds` have passed."""
+def _oracle_prefix(w, W):
+    """The FP64 oracle's state after W untimed steps (the start of the GPU's timed window)."""
     from oracle import problem as oprob, pttebd
     cis = oprob.build_inputs(w)
-    done, t_all = 0, 0.0
     states = [pttebd.product_state(ci.rho0) if ci.init_mps is None else ci.init_mps.copy() for ci in cis]
-    for k in range(1, max_steps + 1):
+    for k in range(1, W + 1):
+        for ci, m in zip(cis, states):
+            pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
+    return cis, states
+
+
+def _oracle_timed(w, cis, states, first, seconds, max_steps):
+    """The oracle as it stands: steps first, first+1, .. timed one by one until `seconds` have passed
+    (at least one step) or max_steps were taken."""
+    from oracle import pttebd
+    done, t_all = 0, 0.0
+    for k in range(first, first + max_steps):
         t0 = time.perf_counter()
         for ci, m in zip(cis, states):
             pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
         t_all += time.perf_counter() - t0
-        done = k
+        done += 1
         if t_all > seconds:
             break
     return done, t_all, sum(ci.N for ci in cis)
 
 
-def cpu_baseline(w, seconds):
-    """The oracle as it stands on the host cores over the first steps of the trajectory (a bounded,
-    labelled per-step rate: these early steps are the cheapest, so the rate is an upper bound for the
-    GPU's window), plus the same with one BLAS thread."""
+def cpu_baseline(w, seconds, W, K):
+    """The oracle as it stands on the host cores, on the GPU's own window: its state after the W
+    warm-up steps, then steps W+1.. timed until `seconds` have passed (a bounded sample of the same
+    steps), plus the same sample with one BLAS thread (a subprocess starting from that state)."""
+    import pickle
+    import tempfile
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    done, t_all, N = _oracle_steps(w, seconds, w.K)
-    out = {"value": N * done / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"steps 1..{done} of {w.name} from t = 0 (per-step rate of the first steps; numpy/LAPACK, "
-                     f"{cores} host threads available)"}
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import sys, json; sys.path.insert(0, %r); import bench; from workloads import workload; "
-            "d, t, n = bench._oracle_steps(workload(%r), %f, %d); print(json.dumps([d, t, n]))"
-            % (ROOT, w.name, seconds / 2, w.K))
-    try:
-        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
-        d1, t1, n1 = json.loads(r.stdout.strip().splitlines()[-1])
-        out["single_thread"] = {"value": n1 * d1 / t1, "cores": 1, "sample": f"steps 1..{d1}, one BLAS thread"}
-    except Exception as ex:          # reported, not fatal
-        out["single_thread"] = {"value": None, "error": str(ex)[:200]}
+    cis, states = _oracle_prefix(w, W)
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "state.pkl")
+        with open(path, "wb") as f:
+            pickle.dump((cis, [m.copy() for m in states]), f)
+        done, t_all, N = _oracle_timed(w, cis, states, W + 1, seconds, K)
+        out = {"value": N * done / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"steps {W + 1}..{W + done} of {w.name} (the first {done} of the GPU's {K} timed steps, "
+                         f"from the oracle's own state after the {W} warm-up steps; numpy/LAPACK, "
+                         f"{cores} host threads available)"}
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        code = ("import sys, json, pickle; sys.path.insert(0, %r); import bench; from workloads import workload; "
+                "cis, st = pickle.load(open(%r, 'rb')); "
+                "d, t, n = bench._oracle_timed(workload(%r), cis, st, %d, %f, 1); print(json.dumps([d, t, n]))"
+                % (ROOT, path, w.name, W + 1, seconds))
+        try:
+            r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+            d1, t1, n1 = json.loads(r.stdout.strip().splitlines()[-1])
+            out["single_thread"] = {"value": n1 * d1 / t1, "cores": 1,
+                                    "sample": f"step {W + 1} of {w.name}, one BLAS thread"}
+        except Exception as ex:          # reported, not fatal
+            out["single_thread"] = {"value": None, "error": str(ex)[:200]}
     return out
 
 

@@ -203,6 +203,21 @@ size_t pt_svd_scratch_bytes(int m, int n, int batch);
 int pt_svd_f64(const double* A, int m, int n, int batch, double* sigma, double* U, double* V,
                void* scratch, int max_sweeps, void* cuda_stream);
 
+/* Batched complex GEMM of the fast path on the tensor cores (the products of the fast path's bond
+ * SVD, App. A.2 (f)): C_b = opA(A_b) opB(B_b), b < batch, C_b m x n, inner dimension k. Every
+ * matrix is complex double (interleaved re, im), column-major, with the given leading dimension
+ * (in complex elements) and batch stride (in complex elements); op: 0 as stored, 1 transposed,
+ * 2 conjugate transposed. Arithmetic: each row of opA(A) and column of opB(B) is scaled by a power
+ * of two and cut into six BF16 fixed-point slices; slice products accumulate in FP32 on the
+ * tcgen05 tensor cores (exactly for the two leading levels) and are summed in FP64, so C is
+ * accurate to ~1e-12 of max|row of opA(A)| x max|column of opB(B)|. scratch: device workspace of
+ * pt_zgemm_scratch_bytes(m, n, k, batch) bytes. Synchronous. Errors: PT_ERR_ARG (bad sizes, op or
+ * leading dimension, batch > 1024), PT_ERR_DEVICE_TIMEOUT (a bounded pipeline wait expired). */
+size_t pt_zgemm_scratch_bytes(int m, int n, int k, int batch);
+int pt_zgemm_sliced(int opA, int opB, int m, int n, int k, const double* A, int lda, long long strideA,
+                    const double* B, int ldb, long long strideB, double* C, int ldc, long long strideC, int batch,
+                    void* scratch, void* cuda_stream);
+
 /* ---- allocation-free variant of pt_svd_f64 (the paper has no counterpart) ----
  * For callers that cannot allocate device memory: their device memory is owned by another pool
  * (a framework that reserves the GPU up front, a fixed-budget service), or a device allocation is

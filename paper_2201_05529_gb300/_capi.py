@@ -29,7 +29,7 @@ EXPORTS = [
     "pt_tune_cache_lookup", "pt_tune_cache_store",
     "pt_tebd_sync", "pt_tebd_destroy", "pt_tebd_last_error", "pt_tebd_set_timing",
     "pt_tebd_get_timing", "pt_svd_scratch_bytes", "pt_svd_f64", "pt_svd_f64_noalloc",
-    "pt_selftest_grid_barrier",
+    "pt_zgemm_scratch_bytes", "pt_zgemm_sliced", "pt_selftest_grid_barrier",
 ]
 
 
@@ -110,6 +110,11 @@ lib.pt_svd_f64.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.
                            C.c_void_p, C.c_int, C.c_void_p]
 
 
+lib.pt_zgemm_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+lib.pt_zgemm_scratch_bytes.restype = C.c_size_t
+lib.pt_zgemm_sliced.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_longlong,
+                                C.c_void_p, C.c_int, C.c_longlong, C.c_void_p, C.c_int, C.c_longlong, C.c_int,
+                                C.c_void_p, C.c_void_p]
 lib.pt_svd_f64_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_int, C.c_void_p]
 NOALLOC_MAX_BYTES = 16 << 20     # PT_SVD_NOALLOC_MAX_BYTES
@@ -362,6 +367,28 @@ def svd_f64(A, sigma, U, V, scratch, max_sweeps=0, stream=None):
     rc = lib.pt_svd_f64(C.c_void_p(A.data_ptr()), m, n, b, C.c_void_p(sigma.data_ptr()),
                         C.c_void_p(U.data_ptr()), C.c_void_p(V.data_ptr()),
                         C.c_void_p(scratch.data_ptr()), int(max_sweeps), st)
+    _check(rc, None)
+
+
+ZOPS = {"N": 0, "T": 1, "H": 2}
+
+
+def zgemm_scratch_bytes(m, n, k, batch):
+    return int(lib.pt_zgemm_scratch_bytes(int(m), int(n), int(k), int(batch)))
+
+
+def zgemm_sliced(opA, opB, A, B, C_out, m, n, k, scratch, stream=None):
+    """pt_zgemm_sliced on device tensors: C[b] = opA(A[b]) opB(B[b]) (column-major, complex128).
+    A, B, C_out: [batch, cols, rows] contiguous tensors, i.e. each batch entry column-major with its
+    row count as leading dimension; opA/opB in "N", "T", "H"; scratch: uint8 tensor of
+    zgemm_scratch_bytes(m, n, k, batch)."""
+    b = A.shape[0]
+    lda, ldb, ldc = A.shape[2], B.shape[2], C_out.shape[2]
+    st = stream if stream is not None else current_stream_handle()
+    rc = lib.pt_zgemm_sliced(ZOPS[opA], ZOPS[opB], int(m), int(n), int(k), C.c_void_p(A.data_ptr()), lda,
+                             A.shape[1] * A.shape[2], C.c_void_p(B.data_ptr()), ldb, B.shape[1] * B.shape[2],
+                             C.c_void_p(C_out.data_ptr()), ldc, C_out.shape[1] * C_out.shape[2], int(b),
+                             C.c_void_p(scratch.data_ptr()), st)
     _check(rc, None)
 
 

@@ -515,21 +515,27 @@ float time_once(pt_tebd* h, const std::function<void()>& launch) {
   return ms;
 }
 
+// the layer's route from the tune cache, if it holds one that fits
+bool cached_route(pt_tebd* h, const BondWork* work, const std::vector<BondWork>& v, pt_tebd::Route& r) {
+  const bool odd = work == h->d_odd;
+  const int kc = odd ? h->kcap_odd : h->kcap_even, mc = odd ? h->mcap_odd : h->mcap_even;
+  int qr = r.qr, k2 = r.k2;
+  if (!cache_lookup(h->opt.tune_cache, tune_key(h, v, kc, mc), &qr, &k2)) return false;
+  const bool qr_ok = qr == 2 || (qr == 1 && h->qr_smem_cluster > 0) || (qr == 0 && (odd ? h->qr_grid_odd : h->qr_grid_even));
+  const bool k2_ok = k2 == 1 || (odd ? h->hqr_odd : h->hqr_even);
+  if (!qr_ok || !k2_ok) return false;
+  r.qr = qr;
+  r.k2 = k2;
+  r.cached = true;
+  return true;
+}
+
 int tune_layer(pt_tebd* h, const BondWork* work, int n, const std::vector<BondWork>& v, pt_tebd::Route& r) {
+  if (r.cached) return PT_OK;
   const bool odd = work == h->d_odd;
   const int kc = odd ? h->kcap_odd : h->kcap_even, mc = odd ? h->mcap_odd : h->mcap_even;
   const std::string key = tune_key(h, v, kc, mc);
-  int qr = r.qr, k2 = r.k2;
-  if (cache_lookup(h->opt.tune_cache, key, &qr, &k2)) {
-    const bool qr_ok = qr == 2 || (qr == 1 && h->qr_smem_cluster > 0) || (qr == 0 && (odd ? h->qr_grid_odd : h->qr_grid_even));
-    const bool k2_ok = k2 == 1 || (odd ? h->hqr_odd : h->hqr_even);
-    if (qr_ok && k2_ok) {
-      r.qr = qr;
-      r.k2 = k2;
-      r.cached = true;
-      return PT_OK;
-    }
-  }
+  if (cached_route(h, work, v, r)) return PT_OK;     // another layer of the same shape was just timed
   cudaStream_t s = h->stream;
   // outer-block QR candidates (each on freshly built blocks; the faster of two runs)
   std::vector<int> k2c{1};
@@ -612,6 +618,10 @@ int choose_routes(pt_tebd* h, const std::vector<BondWork>& odd, const std::vecto
     return PT_OK;
   }
   if (!h->opt.autotune || h->grid_blocks <= 0) return PT_OK;
+  // layers the cache answers need no timing; the synthetic state only when one does
+  const bool hit_odd = h->n_odd == 0 || cached_route(h, h->d_odd, odd, h->route_odd);
+  const bool hit_even = h->n_even == 0 || cached_route(h, h->d_even, even, h->route_even);
+  if (hit_odd && hit_even) return PT_OK;
   // synthetic state at capacity
   Tables& T = h->T;
   cudaMemcpyAsync(T.site_kappa, h->kcap_h.data(), sizeof(int) * h->n_sites, cudaMemcpyHostToDevice, h->stream);
@@ -1400,6 +1410,87 @@ size_t pt_svd_scratch_bytes(int m, int n, int batch) {
   if (m < 1 || n < 1 || batch < 1) return 0;
   size_t offs[8];
   return svd_layout(m, n, batch, offs);
+}
+
+static size_t zgemm_layout(int m, int n, int k, int batch, size_t* offs) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o += (bytes + 255) & ~size_t(255);
+    return r;
+  };
+  offs[0] = take(sizeof(ptk::ZGemmItem) * (size_t)batch);
+  offs[1] = take(sizeof(int));                                            // status
+  offs[2] = take(ptk::zgemm_pack_bytes(m, k, 0) * (size_t)batch);         // packed A
+  offs[3] = take(ptk::zgemm_pack_bytes(n, k, 1) * (size_t)batch);         // packed B
+  return o;
+}
+
+size_t pt_zgemm_scratch_bytes(int m, int n, int k, int batch) {
+  if (m < 1 || n < 1 || k < 1 || batch < 1) return 0;
+  size_t offs[4];
+  return zgemm_layout(m, n, k, batch, offs);
+}
+
+int pt_zgemm_sliced(int opA, int opB, int m, int n, int k, const double* A, int lda, long long strideA,
+                    const double* B, int ldb, long long strideB, double* C, int ldc, long long strideC, int batch,
+                    void* scratch, void* cuda_stream) {
+  auto bad = [](const char* why) {
+    g_err = std::string("pt_zgemm_sliced: ") + why;
+    return PT_ERR_ARG;
+  };
+  if (m < 1 || n < 1 || k < 1 || batch < 1 || !A || !B || !C || !scratch) return bad("bad arguments");
+  if (opA < 0 || opA > 2 || opB < 0 || opB > 2) return bad("op must be 0 (N), 1 (T) or 2 (H)");
+  if (lda < (opA == 0 ? m : k) || ldb < (opB == 0 ? k : n) || ldc < m) return bad("leading dimension too small");
+  if (batch > 1024) return bad("batch > 1024");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  size_t offs[4];
+  zgemm_layout(m, n, k, batch, offs);
+  char* base = (char*)scratch;
+  ptk::ZGemmItem* items = (ptk::ZGemmItem*)(base + offs[0]);
+  int* status = (int*)(base + offs[1]);
+  const size_t pa = ptk::zgemm_pack_bytes(m, k, 0), pb = ptk::zgemm_pack_bytes(n, k, 1);
+  std::vector<ptk::ZGemmItem> h(batch);
+  for (int b = 0; b < batch; ++b) {
+    ptk::ZGemmItem it{};
+    it.A = (const double2*)A + (size_t)b * strideA;
+    it.B = (const double2*)B + (size_t)b * strideB;
+    it.C = (double2*)C + (size_t)b * strideC;
+    it.lda = lda;
+    it.ldb = ldb;
+    it.ldc = ldc;
+    it.M = m;
+    it.N = n;
+    it.K = k;
+    it.opA = opA;
+    it.opB = opB;
+    it.TA = (unsigned char*)(base + offs[2]) + (size_t)b * pa;
+    it.TB = (unsigned char*)(base + offs[3]) + (size_t)b * pb;
+    it.cap_m = m;
+    it.cap_n = n;
+    it.cap_k = k;
+    h[b] = it;
+  }
+  cudaMemcpyAsync(items, h.data(), sizeof(ptk::ZGemmItem) * batch, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(status, 0, sizeof(int), st);
+  ptk::launch_zgemm(items, batch, ptk::zgemm_tile_cap(m, n) * batch, m, n, status, st);
+  int hs = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);      // also keeps h alive for the copy above
+  if (e != cudaSuccess) {
+    g_err = std::string("pt_zgemm_sliced: ") + cudaGetErrorString(e);
+    return PT_ERR_CUDA;
+  }
+  if (hs & ST_TIMEOUT) {
+    g_err = "pt_zgemm_sliced: an mbarrier wait ran out of time";
+    return PT_ERR_DEVICE_TIMEOUT;
+  }
+  if (hs & ST_CAPACITY) {
+    g_err = "pt_zgemm_sliced: capacity";
+    return PT_ERR_CAPACITY;
+  }
+  return PT_OK;
 }
 
 int pt_svd_f64(const double* A, int m, int n, int batch, double* sigma, double* U, double* V,

@@ -83,6 +83,31 @@ int tc_tile_cap(const BondWork& W, int precision);
 void launch_tc_theta(const Tables& T, const BondWork* work, int n_work, int tile_cap, int precision,
                      cudaStream_t st);
 
+// batched complex GEMM on the tensor cores with an FP64-class result (tc_zgemm.cu):
+// C = opA(A) opB(B), M x N, inner dimension K, per item; live dims in device memory (M, N or K = 0:
+// the item is skipped and C left untouched). TA / TB: the item's packed operands, sized by
+// zgemm_pack_bytes for its capacities (cap_m x cap_k for A, cap_n x cap_k for B).
+enum : int { ZOP_N = 0, ZOP_T = 1, ZOP_C = 2 };
+struct ZGemmItem {
+  const double2* A;
+  const double2* B;
+  double2* C;
+  int lda, ldb, ldc;
+  int M, N, K;
+  int opA, opB;            // ZOP_N as stored (column-major), ZOP_T transposed, ZOP_C conjugate transpose
+  const int* bcol;         // column n of opB(B) is its stored column bcol[n] (NULL: n)
+  unsigned char* TA;
+  unsigned char* TB;
+  int cap_m, cap_n, cap_k;
+  int* flag;               // set to 1 when a product entry is not finite (NULL: not reported)
+};
+size_t zgemm_pack_bytes(int rows_cap, int k_cap, int which);
+int zgemm_tile_cap(int m_cap, int n_cap);
+// tile_cap: total output tiles of the item list at capacity (the persistent grid's upper bound);
+// m_cap_max / n_cap_max: the largest M and N capacities (pack grid sizes)
+void launch_zgemm(const ZGemmItem* items, int n_items, int tile_cap, int m_cap_max, int n_cap_max, int* status,
+                  cudaStream_t st);
+
 // set the message returned by pt_tebd_last_error(NULL) (engine.cu)
 void set_global_error(const char* msg);
 
