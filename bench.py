@@ -241,7 +241,8 @@ def _secondary(capi, pp, workload, torch, stream, flush, prec, W=5, K=20):
     out = {"workload": w.name, "window": f"steps {W}..{W + K} of {w.K}"}
     hist = {}
     for p in (prec, "fp64"):
-        e = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, precision=p, max_steps=w.K, use_graph=True)
+        e = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, precision=p, multiplet_tol=w.multiplet_tol,
+                        max_steps=w.K, use_graph=True)
         e.set_observables([pp.pauli("z")])
         e.step(W)
         ms = _timed_window(e, K, stream, flush, torch)
@@ -274,7 +275,7 @@ def run_ours(args, rank, world, local):
 
     def make(precision, graph=True):
         e = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, precision=precision,
-                        max_steps=w.K, use_graph=graph)
+                        multiplet_tol=w.multiplet_tol, max_steps=w.K, use_graph=graph)
         e.set_observables([Z])
         return e
 
@@ -433,7 +434,7 @@ def _oracle_prefix(w, W):
     states = [pttebd.product_state(ci.rho0) if ci.init_mps is None else ci.init_mps.copy() for ci in cis]
     for k in range(1, W + 1):
         for ci, m in zip(cis, states):
-            pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
+            pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps, multiplet_tol=w.multiplet_tol)
     return cis, states
 
 
@@ -445,7 +446,7 @@ def _oracle_timed(w, cis, states, first, seconds, max_steps):
     for k in range(first, first + max_steps):
         t0 = time.perf_counter()
         for ci, m in zip(cis, states):
-            pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
+            pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps, multiplet_tol=w.multiplet_tol)
         t_all += time.perf_counter() - t0
         done += 1
         if t_all > seconds:
@@ -501,14 +502,15 @@ def run_reference(args, rank, world):
     for ci in cis:
         m = pttebd.product_state(ci.rho0) if ci.init_mps is None else ci.init_mps.copy()
         for k in range(1, W + 1):
-            pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
+            pttebd.pt_step(m, k, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps, multiplet_tol=w.multiplet_tol)
         states.append(m)
     ms = []
     t_all = 0.0
     for i in range(K):
         ts = time.perf_counter()
         for ci, m in zip(cis, states):
-            pttebd.pt_step(m, W + i + 1, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps)
+            pttebd.pt_step(m, W + i + 1, ci.gates_q, ci.gates_h, ci.pt, w.chi_max, w.eps,
+                           multiplet_tol=w.multiplet_tol)
         ms.append((time.perf_counter() - ts) * 1e3)
         t_all += ms[-1] / 1e3
         if t_all > args.ref_seconds:

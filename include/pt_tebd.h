@@ -55,10 +55,17 @@ typedef enum {
                        accumulation to ~1e-6 relative); FP64 SVD, truncation and readout */
   PT_BF16X3 = 2,    /* the same with three BF16 pieces (~24 significant bits) */
   PT_TF32X1 = 3,    /* one TF32 piece, one product (speed reference only) */
-  PT_BF16_OZAKI = 4 /* the theta contraction from fixed-point BF16 slices: each operand row scaled by
-                       a power of two and cut into five slices, so the leading slice products sum
-                       exactly in the tensor cores' FP32 accumulators (Ozaki's error-free splitting);
-                       ~1e-9 relative to the rows' scale; FP64 SVD, truncation and readout */
+  PT_BF16_OZAKI = 4 /* the fast path: every large product on the tensor cores from fixed-point BF16
+                       slices (each operand row / column scaled by a power of two and cut into six
+                       7-bit slices; the leading slice products sum exactly in FP32 accumulators over
+                       K chunks of 512, Ozaki's error-free splitting; ~1e-12 of the operands' scale).
+                       theta + gate is one such GEMM; the bond SVD is a randomized truncated SVD
+                       (range finder of width l = min(n, chi_max + 32) with one power iteration, its
+                       products on the tensor cores, FP64 Householder QR and an FP64 Jacobi SVD of
+                       the l x l factor; the part of D outside the range counts as one discarded
+                       singular value). Its singular values are accurate to ~1e-11 of sigma_max, so
+                       the multiplet rule uses max(multiplet_tol, 1e-9). Truncation, Gamma recovery
+                       and readout in FP64 */
 } pt_precision;
 
 /* One chain (App. A.1). Sites without a bath have ptmpo_id = -1 (augmented leg of dimension 1).

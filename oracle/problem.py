@@ -125,14 +125,17 @@ class RunResult:
 
 
 def simulate_chain(ci: ChainInputs, w, ops, K=None, variant="qr", normalize=False,
-                   insert=None, multiplet_tol=MULTIPLET_TOL, keep_lambdas=False, insert_at=0):
+                   insert=None, multiplet_tol=None, keep_lambdas=False, insert_at=0):
     """Run the PT-TEBD schedule for one chain; observe every op on every site after each step.
 
     insert = (site, 2x2 operator, 'left'|'right') applies that super-operator to the full augmented
     MPS after step insert_at (0: the initial state), before that step's readout (App. A.4; the
     branching at a later time follows the two-time correlation procedure of App. B.2).
+    multiplet_tol: the truncation's multiplet tolerance (None: the workload's).
     """
     K = w.K if K is None else K
+    if multiplet_tol is None:
+        multiplet_tol = getattr(w, "multiplet_tol", MULTIPLET_TOL)
     m = ci.init_mps.copy() if ci.init_mps is not None else pttebd.product_state(ci.rho0)
     site_caps = []
     for n in range(ci.N):

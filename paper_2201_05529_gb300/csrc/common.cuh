@@ -32,6 +32,17 @@ PT_DEV double2 cfma_conj(double2 a, double2 b, double2 acc) {
 }
 PT_DEV double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
+// counter-based hash -> a value in (-1, 1): a 64-bit finaliser of the counter (no state, the same
+// value for the same counter on every launch)
+PT_DEV double hash_unit(unsigned long long x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdULL;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ULL;
+  x ^= x >> 33;
+  return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
 // ---------------------------------------------------------------- device status word codes
 enum : int {
   ST_OK = 0,
@@ -97,15 +108,23 @@ struct BondWork {
   int* perm;               // [k_cap] perm[rank] = column
   void* TA;                // fast path: packed split planes of the theta operands (tc_theta.cu)
   void* TB;
-  float2* A32;             // fast path: FP32 copy of D for the bulk Jacobi sweeps
-  float2* V32;             // fast path: FP32 right factor of those sweeps
-  double2* G64;            // fast path: [k_cap^2] Gram / product scratch of the V re-orthonormalisation
+  double2* G64;            // [k_cap^2] B = R^H of the pivoted QR; fast path: the range finder's l x l factor
   double2* Y64;            // [max(mD,nD)_cap * k_cap] QR workspace / product scratch
   int* qperm;              // [k_cap] column permutation of the pivoted QR
   int* info;               // [16] per-item: 0 mD, 1 nD, 2 transposed, 3 sweeps, 4-5 rotation counters,
                            // 6 fault flags of the update (FAULT_*), 7 NaN flag of theta, 8 rank k of
-                           // the pivoted QR, 10-11 the update's discarded weight (a double)
+                           // the pivoted QR, 9 the range finder's width l, 10-11 the update's
+                           // discarded weight (a double), 12-13 ||D||_F^2 (a double, fast path)
+  // fast path (randomized truncated SVD, rsvd.cu): l <= L_cap columns, rows <= rs_mx
+  double2* RY;             // [rs_mx * L_cap]  Y = D Omega, then Q
+  double2* RZ;             // [k_cap * L_cap]  Z = D^H Q, then Qz / Qb
+  double2* RH;             // [rs_mx * L_cap]  Householder vectors
+  double2* RR;             // [L_cap * L_cap]  discarded triangular factors
+  double* Rtau;            // [L_cap]
+  unsigned char* ZA;       // packed operands of the sliced tensor-core GEMMs
+  unsigned char* ZB;
   int mL_cap, nL_cap, mR_cap, nR_cap, mD_cap, nD_cap, k_cap, pad2;
+  int rs_mx, L_cap;        // max(mD_cap, nD_cap) and the range finder's capacity (0: no fast path)
 };
 
 struct SiteWork {

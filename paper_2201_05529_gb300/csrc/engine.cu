@@ -97,6 +97,11 @@ struct pt_tebd {
   } route_odd, route_even;
   int tune_status = 0;                // device status word seen at the end of the tuning run
   int kcap_odd = 1, kcap_even = 1, mcap_odd = 1, mcap_even = 1;
+  // fast path: the randomized truncated SVD of the bonds (rsvd.cu)
+  bool use_rsvd = false;
+  ptk::RsvdLists rs_odd{}, rs_even{};
+  double2* d_omega = nullptr;         // the range finder's sketch matrix (ld_omega x l_max)
+  int ld_omega = 1;
   unsigned* d_sync3 = nullptr;        // grid barrier state
   int* d_cnt_odd = nullptr;           // per-item rotation counters
   int* d_cnt_even = nullptr;
@@ -239,6 +244,9 @@ void enqueue_qr(pt_tebd* h, const BondWork* work, int n, int qr, int kmax) {
                                   h->T.status, h->stream);
 }
 
+// multiplet floor of the fast path (relative to sigma_max): above its singular values' accuracy
+constexpr double FAST_MULTIPLET_TOL = 1e-9;
+
 void enqueue_layer(pt_tebd* h, const BondWork* work, int n, int layer) {
   if (n == 0) return;
   cudaStream_t s = h->stream;
@@ -256,7 +264,28 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n, int layer) {
   ptk::k_nan_guard<<<(n + 127) / 128, 128, 0, s>>>(h->T, work, n);
   ev_end(h, e);
   int* cnt = work == h->d_odd ? h->d_cnt_odd : h->d_cnt_even;
-  if (h->grid_blocks > 0) {
+  if (h->use_rsvd) {
+    // fast path: randomized truncated SVD (tensor-core products, whole-GPU QR and l x l Jacobi)
+    const ptk::RsvdLists& L = work == h->d_odd ? h->rs_odd : h->rs_even;
+    ev_begin(h, 8, &e);
+    ptk::launch_rsvd(h->T, work, n, L, h->opt.chi_max, ptk::RSVD_OVERSAMPLE, h->d_omega, h->ld_omega,
+                     h->grid_blocks, h->d_sync3, s);
+    ev_end(h, e);
+    ev_begin(h, 3, &e);
+    const double tol_scale = 9.007199254740992e6;     // |cos| <= 1e-9, below the products' accuracy
+    ptk::launch_jacobi_grid(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status, s, 1, 1,
+                            1.1102230246251565e-16, 3, /*on_b=*/2, /*with_v=*/1, tol_scale);
+    ev_end(h, e);
+    ev_begin(h, 4, &e);
+    // the fast path's singular values carry errors of ~1e-11 of sigma_max: gaps below the
+    // FAST_MULTIPLET_TOL floor count as degenerate, so it sees the exact multiplets the FP64 path sees
+    const double mtol = std::max(h->opt.multiplet_tol, FAST_MULTIPLET_TOL);
+    ptk::k_truncate<<<(n + 63) / 64, 64, 0, s>>>(h->T, work, n, h->opt.chi_max, h->opt.eps, mtol, /*rsvd=*/1);
+    ev_end(h, e);
+    ev_begin(h, 8, &e);
+    ptk::launch_rsvd_vectors(h->T, work, n, L, s);
+    ev_end(h, e);
+  } else if (h->grid_blocks > 0) {
     // QR-preconditioned FP64 Jacobi: pivoted QR, Jacobi on R^H, then V_D = P U', U_D = D V_D / sigma
     const int kc = work == h->d_odd ? h->kcap_odd : h->kcap_even, mc = work == h->d_odd ? h->mcap_odd : h->mcap_even;
     ev_begin(h, 8, &e);
@@ -277,11 +306,13 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n, int layer) {
                                h->T.status, s);
     ev_end(h, e);
   }
-  ev_begin(h, 4, &e);
-  ptk::k_truncate<<<(n + 63) / 64, 64, 0, s>>>(h->T, work, n, h->opt.chi_max, h->opt.eps,
-                                                h->opt.multiplet_tol);
-  ev_end(h, e);
-  if (h->grid_blocks > 0) {
+  if (!h->use_rsvd) {
+    ev_begin(h, 4, &e);
+    ptk::k_truncate<<<(n + 63) / 64, 64, 0, s>>>(h->T, work, n, h->opt.chi_max, h->opt.eps,
+                                                  h->opt.multiplet_tol);
+    ev_end(h, e);
+  }
+  if (!h->use_rsvd && h->grid_blocks > 0) {
     // the SVD's finish on the kept columns only: V_D = P U', U_D = D V_D / sigma
     const int kc = work == h->d_odd ? h->kcap_odd : h->kcap_even, mc = work == h->d_odd ? h->mcap_odd : h->mcap_even;
     ev_begin(h, 8, &e);
@@ -554,24 +585,29 @@ int tune_layer(pt_tebd* h, const BondWork* work, int n, const std::vector<BondWo
     if (r.ms_k2[c] < r.ms_k2[r.k2]) r.k2 = c;
   // D of the synthetic state, then the pivoted-QR candidates on it (a 128-reflector prefix each;
   // every candidate reads D and writes only its own workspace)
-  ptk::k_build_blocks<<<dim3(h->gx_bond, n), 256, 0, s>>>(h->T, work, n);
-  enqueue_k2(h, work, n, r.k2);
-  if (h->opt.precision == PT_FP64)
-    ptk::k_theta_gate<<<dim3(h->gx_bond, n), 128, 0, s>>>(h->T, work, n);
-  else
-    ptk::launch_tc_theta(h->T, work, n, odd ? h->tiles_odd : h->tiles_even, (int)h->opt.precision, s);
+  if (!h->use_rsvd) {
+    ptk::k_build_blocks<<<dim3(h->gx_bond, n), 256, 0, s>>>(h->T, work, n);
+    enqueue_k2(h, work, n, r.k2);
+    if (h->opt.precision == PT_FP64)
+      ptk::k_theta_gate<<<dim3(h->gx_bond, n), 128, 0, s>>>(h->T, work, n);
+    else
+      ptk::launch_tc_theta(h->T, work, n, odd ? h->tiles_odd : h->tiles_even, (int)h->opt.precision, s);
+  }
   std::vector<int> qrc{2};
-  if (h->qr_smem_cluster > 0) qrc.insert(qrc.begin(), 1);
-  if (odd ? h->qr_grid_odd : h->qr_grid_even) qrc.insert(qrc.begin(), 0);
+  if (h->use_rsvd) qrc.clear();                      // the fast path's SVD has no pivoted QR
+  else if (h->qr_smem_cluster > 0) qrc.insert(qrc.begin(), 1);
+  if (!h->use_rsvd && (odd ? h->qr_grid_odd : h->qr_grid_even)) qrc.insert(qrc.begin(), 0);
   for (int c : qrc) {
     float best = 1e30f;
     for (int rep = 0; rep < 2; ++rep)
       best = std::min(best, time_once(h, [&] { enqueue_qr(h, work, n, c, std::min(kc, 128)); }));
     r.ms_qr[c] = best;
   }
-  r.qr = qrc[0];
-  for (int c : qrc)
-    if (r.ms_qr[c] < r.ms_qr[r.qr]) r.qr = c;
+  if (!qrc.empty()) {
+    r.qr = qrc[0];
+    for (int c : qrc)
+      if (r.ms_qr[c] < r.ms_qr[r.qr]) r.qr = c;
+  }
   r.tuned = true;
   int rc = check_cuda(h, "autotune");
   if (rc == PT_OK) cache_store(h->opt.tune_cache, key, r);
@@ -892,9 +928,25 @@ int build(pt_tebd* h) {
       if (h->opt.precision != PT_FP64) {
         W.TA = h->dalloc(ptk::tc_pack_bytes(W, 0, (int)h->opt.precision));
         W.TB = h->dalloc(ptk::tc_pack_bytes(W, 1, (int)h->opt.precision));
-        W.A32 = (float2*)h->dalloc(sizeof(float2) * as);
-        W.V32 = (float2*)h->dalloc(sizeof(float2) * vs);
-        if (!W.TA || !W.TB || !W.A32 || !W.V32) return h->fail(PT_ERR_OOM, "fast-path scratch");
+        if (!W.TA || !W.TB) return h->fail(PT_ERR_OOM, "fast-path scratch");
+      }
+      if (h->opt.precision == PT_BF16_OZAKI) {
+        // the randomized truncated SVD: l <= chi_max + oversampling columns
+        W.rs_mx = std::max(W.mD_cap, W.nD_cap);
+        W.L_cap = std::max(1, std::min(W.k_cap, h->opt.chi_max + ptk::RSVD_OVERSAMPLE));
+        const size_t L = (size_t)W.L_cap;
+        W.RY = (double2*)h->dalloc(sizeof(double2) * W.rs_mx * L);
+        W.RZ = (double2*)h->dalloc(sizeof(double2) * W.k_cap * L);
+        W.RH = (double2*)h->dalloc(sizeof(double2) * W.rs_mx * L);
+        W.RR = (double2*)h->dalloc(sizeof(double2) * L * L);
+        W.Rtau = (double*)h->dalloc(sizeof(double) * L);
+        W.ZA = (unsigned char*)h->dalloc(ptk::zgemm_pack_bytes(W.rs_mx, W.rs_mx, 0));
+        // B operands: up to L_cap columns with K up to rs_mx, or (the residual D - Q Z^H) up to
+        // rs_mx columns with K up to L_cap
+        W.ZB = (unsigned char*)h->dalloc(std::max(ptk::zgemm_pack_bytes(W.L_cap, W.rs_mx, 1),
+                                                  ptk::zgemm_pack_bytes(W.rs_mx, W.L_cap, 1)));
+        if (!W.RY || !W.RZ || !W.RH || !W.RR || !W.Rtau || !W.ZA || !W.ZB)
+          return h->fail(PT_ERR_OOM, "fast-path SVD scratch");
       }
       {
         const size_t ma = (size_t)std::max(W.mD_cap, W.nD_cap);
@@ -976,6 +1028,41 @@ int build(pt_tebd* h) {
     };
     defaults(h->route_odd, h->qr_grid_odd, h->hqr_odd);
     defaults(h->route_even, h->qr_grid_even, h->hqr_even);
+  }
+  if (h->opt.precision == PT_BF16_OZAKI && h->grid_blocks > 0 && ptk::hqr_items_ok()) {
+    // the fast path's randomized truncated SVD: item lists per layer, the sketch matrix
+    auto lists = [&](const std::vector<BondWork>& v, ptk::RsvdLists& L) {
+      const int n = std::max<int>(1, (int)v.size());
+      long long cols = 0, tiles = 0;
+      L.m_cap = L.l_cap = 1;
+      for (auto& W : v) {
+        cols += W.L_cap;
+        tiles += ptk::zgemm_tile_cap(W.rs_mx, W.L_cap);
+        L.m_cap = std::max(L.m_cap, W.rs_mx);
+        L.l_cap = std::max(L.l_cap, W.L_cap);
+      }
+      L.tile_cap = (int)std::min<long long>(tiles, 1 << 30);
+      ptk::ZGemmItem** z[7] = {&L.gy1, &L.gz1, &L.gy2, &L.gz2, &L.gres, &L.gu, &L.gv};
+      for (auto p : z) *p = (ptk::ZGemmItem*)h->dalloc(sizeof(ptk::ZGemmItem) * n);
+      ptk::QRItem** q[4] = {&L.q1, &L.qz, &L.q2, &L.qb};
+      for (auto p : q) *p = (ptk::QRItem*)h->dalloc(sizeof(ptk::QRItem) * n);
+      bool ok = true;
+      for (auto p : z) ok = ok && *p;
+      for (auto p : q) ok = ok && *p;
+      return ok && cols <= (long long)h->grid_blocks * 384;
+    };
+    bool ok = lists(odd, h->rs_odd) && lists(even, h->rs_even);
+    int rows = 1, cols = 1;
+    for (auto* v : {&odd, &even})
+      for (auto& W : *v) {
+        rows = std::max(rows, W.k_cap);
+        cols = std::max(cols, W.L_cap);
+      }
+    h->ld_omega = rows;
+    h->d_omega = (double2*)h->dalloc(sizeof(double2) * (size_t)rows * cols);
+    if (!h->d_omega) return h->fail(PT_ERR_OOM, "fast-path sketch matrix");
+    ptk::launch_rsvd_omega(h->d_omega, rows, cols, 20220113u, h->stream);
+    h->use_rsvd = ok;
   }
   h->d_sync3 = (unsigned*)h->dalloc(sizeof(unsigned) * 4);
   h->d_cnt_odd = (int*)h->dalloc(sizeof(int) * 2 * std::max(1, h->n_odd));

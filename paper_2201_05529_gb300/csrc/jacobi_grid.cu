@@ -11,8 +11,9 @@
 // reproducible. Every barrier wait has a time limit: on expiry the kernel records ST_TIMEOUT,
 // raises an abort flag that releases every other CTA, and returns.
 //
-// on_b: the matrix is the square R^H left by the pivoted QR (qrcp.cu); only its left vectors are
-// wanted there, so the right factor is not accumulated.
+// on_b = 1: the matrix is R^H left by the pivoted QR (qrcp.cu); only its left vectors are wanted
+// there, so the right factor is not accumulated. on_b = 2: the l x l triangular factor of the fast
+// path's randomized range finder (rsvd.cu), both factors wanted.
 #include <climits>
 
 #include "grid_sync.cuh"
@@ -231,8 +232,9 @@ __device__ __forceinline__ void process_pair(typename Cx<R>::T* A, typename Cx<R
 }
 
 // One-sided Jacobi over all matrices of a layer in FP64: on W.A (or on B = R^H in G64) with V in
-// W.V. on_b: the matrix
-// is the pivoted QR's B = R^H, Na rows and info[8] columns. with_v: accumulate the right factor V
+// W.V. on_b = 1: the matrix
+// is the pivoted QR's B = R^H, Na rows and info[8] columns; on_b = 2: the l x l factor in G64,
+// l = info[9]. with_v: accumulate the right factor V
 // (from V = I when init_v). finalize: write sigma, the normalised left vectors and the order.
 // floor_eps: unit roundoff that sets the noise floor; tol_scale: a pair rotates while
 // |a_i^H a_j| > tol_scale * unit roundoff * |a_i| |a_j| (0: the row count m; < 0: 4 sqrt(m), the
@@ -267,12 +269,12 @@ __global__ void __launch_bounds__(GRID_THREADS)
   for (int w = tid; w < n_work; w += blockDim.x) {
     int Ma, Na;
     item_shape(work[w], &Ma, &Na);
-    // on_b: B = R^H of the pivoted QR (G64), Na rows and k = info[8] columns (the QR's rank)
-    const int kq = on_b ? max(0, min(work[w].info[8], Na)) : Na;
-    s_Nf[w] = Na;
+    // on_b = 1: B = R^H of the pivoted QR (G64), Na rows and k = info[8] columns (the QR's rank);
+    // on_b = 2: the range finder's small square factor (G64), l = info[9] rows and columns
+    const int kq = on_b == 1 ? max(0, min(work[w].info[8], Na)) : (on_b == 2 ? max(0, min(work[w].info[9], Na)) : Na);
+    s_Nf[w] = on_b == 2 ? kq : Na;
     s_Na[w] = kq;
-    s_Ma[w] = Na;
-    if (!on_b) s_Ma[w] = Ma;
+    s_Ma[w] = on_b == 1 ? Na : (on_b == 2 ? kq : Ma);
     s_active[w] = kq >= 2;
     s_A[w] = on_b ? Cx<R>::B(work[w]) : Cx<R>::A(work[w]);
     s_V[w] = Cx<R>::V(work[w]);

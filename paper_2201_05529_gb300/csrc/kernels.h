@@ -19,8 +19,10 @@ __global__ void k_bond_log(Tables T, const BondWork* work, int n_work, int layer
 // the autotuner's synthetic full-capacity state: every Gamma at capacity filled with seeded values
 // in (-1, 1), every lambda with a decaying unit-norm profile (dims set by the host beforehand)
 __global__ void k_tune_fill(Tables T, int n_sites, int n_lams, unsigned seed);
+// rsvd: the singular values are the range finder's l = info[9] values, plus the part of D outside
+// its subspace as one lumped value ||D - Q Q^H D||_F (info[12..13]) when l < min(m, n)
 __global__ void k_truncate(Tables T, const BondWork* work, int n_work, int chi_max, double eps,
-                           double mtol);
+                           double mtol, int rsvd = 0);
 __global__ void k_recover(Tables T, const BondWork* work, int n_work);
 __global__ void k_caps(Tables T, int n_mpos);
 __global__ void k_observe_m(Tables T, int n_chains, double2* Mbuf, const size_t* moff);
@@ -34,7 +36,18 @@ __global__ void k_svd_store(const double2* work_A, const double2* work_V, const 
                             const int* perm, int m, int n, int batch, size_t strideA,
                             size_t strideV, double* sigma_out, double2* U, double2* V);
 
-// whole-GPU Householder QR/LQ of the outer blocks of every bond of a layer (hqr_grid.cu)
+// whole-GPU Householder QR/LQ of the outer blocks of every bond of a layer (hqr_grid.cu), and the
+// same factorisation over a list of matrices: A (m x n, m >= n, column-major, ld m) is replaced by
+// the explicit Q, R (n x n, ld n) receives the triangular factor, H (m x n) and tau (n) are scratch
+struct QRItem {
+  double2* A;
+  double2* H;
+  double2* R;
+  double* tau;
+  int m, n;
+};
+void launch_hqr_items(const QRItem* items, int n_items, int blocks, unsigned* sync3, int* status, cudaStream_t st);
+int hqr_items_ok();
 int hqr_grid_ok();
 int hqr_grid_fits(int total_cols_cap, int n_items, int blocks);
 void launch_hqr_grid(const Tables& T, const BondWork* work, int n_work, int blocks, unsigned* sync3,
@@ -50,7 +63,8 @@ void launch_jacobi_cluster(const BondWork* work, int n_work, int cluster, int ma
 int jacobi_grid_blocks();
 // init_v: start from V = I; finalize: sigma, U, order; floor_eps: unit roundoff of the noise floor;
 // sweep_slot: info[] index for the sweep count
-// on_b: B = R^H of the pivoted QR (Na x info[8]); with_v: accumulate V; tol_scale: rotation threshold
+// on_b: 1 = B = R^H of the pivoted QR (Na x info[8]), 2 = the range finder's l x l factor in G64
+// (l = info[9]); with_v: accumulate V; tol_scale: rotation threshold
 // in units of the unit roundoff (0: the row count)
 void launch_jacobi_grid(const BondWork* work, int n_work, int blocks, int max_sweeps, unsigned* sync3,
                         int* cnt, int* status, cudaStream_t st, int init_v = 1, int finalize = 1,
@@ -100,6 +114,7 @@ struct ZGemmItem {
   unsigned char* TB;
   int cap_m, cap_n, cap_k;
   int* flag;               // set to 1 when a product entry is not finite (NULL: not reported)
+  int acc;                 // 0: C = opA(A) opB(B); -1: C = C - opA(A) opB(B)
 };
 size_t zgemm_pack_bytes(int rows_cap, int k_cap, int which);
 int zgemm_tile_cap(int m_cap, int n_cap);
@@ -107,6 +122,24 @@ int zgemm_tile_cap(int m_cap, int n_cap);
 // m_cap_max / n_cap_max: the largest M and N capacities (pack grid sizes)
 void launch_zgemm(const ZGemmItem* items, int n_items, int tile_cap, int m_cap_max, int n_cap_max, int* status,
                   cudaStream_t st);
+
+// the fast path's randomized truncated SVD of every bond of a layer (rsvd.cu): device item lists
+// (one entry per bond each) and their launch capacities
+struct RsvdLists {
+  ZGemmItem *gy1, *gz1, *gy2, *gz2, *gres, *gu, *gv;
+  QRItem *q1, *qz, *q2, *qb;
+  int tile_cap;            // output tiles of one product over the layer at capacity
+  int m_cap, l_cap;        // largest row count and range-finder width of the layer's bonds
+};
+constexpr int RSVD_OVERSAMPLE = 32;
+// power iterations: the subspace error at the cut chi falls like (s_{l+1} / s_chi)^(2q+1)
+constexpr int RSVD_POWER = 2;
+void launch_rsvd_omega(double2* Om, int rows, int cols, unsigned seed, cudaStream_t st);
+// the range finder up to the l x l factor in G64 (then: the Jacobi on it, launch_jacobi_grid with
+// on_b = 2; the truncation, k_truncate with rsvd = 1; the kept singular vectors into A and V)
+void launch_rsvd(const Tables& T, const BondWork* work, int n_work, const RsvdLists& L, int chi_max, int p,
+                 const double2* Om, int ld_om, int blocks, unsigned* sync3, cudaStream_t st);
+void launch_rsvd_vectors(const Tables& T, const BondWork* work, int n_work, const RsvdLists& L, cudaStream_t st);
 
 // set the message returned by pt_tebd_last_error(NULL) (engine.cu)
 void set_global_error(const char* msg);

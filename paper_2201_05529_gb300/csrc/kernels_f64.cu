@@ -333,13 +333,26 @@ PT_DEV int truncation_rank(const double* sig, const int* perm, int n, double eps
 }
 
 __global__ void k_truncate(Tables T, const BondWork* work, int n_work, int chi_max, double eps,
-                           double mtol) {
+                           double mtol, int rsvd) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= n_work) return;
   const BondWork& W = work[w];
   const int mD = W.info[0], nD = W.info[1];
   if (mD <= 0 || nD <= 0) return;
-  const int n = min(mD, nD);
+  int n = min(mD, nD);
+  if (rsvd) {
+    // the fast path's range finder: l computed values; what lies outside its subspace is one
+    // lumped value (never kept: chi <= chi_max < l whenever l < n)
+    const int l = W.info[9];
+    if (l <= 0) return;
+    if (l < n) {
+      W.sig[l] = sqrt(fmax(0.0, *(const double*)(W.info + 12)));     // ||D - Q Q^H D||_F
+      W.perm[l] = l;
+      n = l + 1;
+    } else {
+      n = l;
+    }
+  }
   const int BC = W.lam_l + 1;
   int chi = truncation_rank(W.sig, W.perm, n, eps, chi_max, mtol);
   if (chi > T.lam_cap[BC]) {
@@ -391,17 +404,6 @@ __global__ void k_bond_log(Tables T, const BondWork* work, int n_work, int layer
 }
 
 // ------------------------------------------------------------------ autotuner's synthetic state
-// A counter-based hash (a 64-bit finaliser) gives every entry a value in (-1, 1): no state, the same
-// values for the same (seed, site, index) on every launch.
-PT_DEV double hash_unit(unsigned long long x) {
-  x ^= x >> 33;
-  x *= 0xff51afd7ed558ccdULL;
-  x ^= x >> 33;
-  x *= 0xc4ceb9fe1a85ec53ULL;
-  x ^= x >> 33;
-  return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
-}
-
 __global__ void k_tune_fill(Tables T, int n_sites, int n_lams, unsigned seed) {
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
   for (int s = 0; s < n_sites; ++s) {

@@ -9,14 +9,15 @@
 //
 // Arithmetic (the error-free splitting of Ozaki, Ogita, Oishi and Rump, as in the theta GEMM):
 // every row of opA(A) and every column of opB(B) is scaled by a power of two 2^-e so its entries
-// lie in (-1, 1), then cut into six BF16 fixed-point slices a_s 2^(-b(s+1)) with integer
-// |a_s| <= 2^b (b = 7 up to K = 512, 6 up to 2048, 5 beyond). Slice products are exact in FP32 and
-// the level-0 and level-1 sums over K stay integers below 2^24, so the tensor cores' FP32
-// accumulation is exact there; the deeper levels carry only their own rounding. Products of slice
+// lie in (-1, 1), then cut into six BF16 fixed-point slices a_s 2^(-7(s+1)) with integer
+// |a_s| <= 2^7. Slice products are exact in FP32, and K is accumulated in chunks of 512 so that the
+// level-0 and level-1 sums of a chunk stay integers below 2^24: the tensor cores' FP32 accumulation
+// is exact there, the deeper levels carry only their own rounding, and the chunks are added in
+// FP64 in the output. Products of slice
 // pairs (s, t) accumulate in TMEM by level min(s + t, 3), real and imaginary parts separately
 // (Re = Ar Br - Ai Bi via the MMA's negate-A bit, Im = Ar Bi + Ai Br); the epilogue adds the
 // levels in FP64 and applies 2^(e_row + e_col). The result is accurate to ~1e-12 of the scale
-// of the rows and columns it combines.
+// of the rows and columns it combines (per 512-long chunk of K).
 //
 // Data flow: two passes per operand (row exponents, then the 12 slice planes in the tcgen05
 // K-major no-swizzle layout: A in 128-row tiles, B in 64-column tiles, one 16-element K step per
@@ -39,6 +40,8 @@ using namespace tcx;
 namespace {
 
 constexpr int ZNS = 6;                        // BF16 slices per value
+constexpr int ZBITS = 7;                      // slice width
+constexpr int ZKC_STEPS = 32;                 // K steps (16 each) per exact accumulation chunk: K = 512
 using ZG = Geo<true>;                         // BF16 geometry: 16-element K steps
 
 __host__ __device__ __forceinline__ PackCap zcap(const ZGemmItem& it, int which) {
@@ -110,28 +113,29 @@ __global__ void k_zg_pack(const ZGemmItem* items, int n_items, int which, int* s
     return;
   }
   const int rows = which == 0 ? it.M : it.N, tr = which == 0 ? TMA : TNB;
+  constexpr int NS = ZNS;
   const PackCap cp = zcap(it, which);
   unsigned char* out = which == 0 ? it.TA : it.TB;
   const int* ex = (const int*)(out + cp.exp_off);
   const int n_rt = cdiv(rows, tr), n_ks = cdiv(it.K, ZG::KSTEP);
   const int padded = n_rt * tr, n_grp = 2 * n_ks;
-  const int b = slice_bits(it.K);
+  const int b = ZBITS;         // the GEMM accumulates K in chunks of 512: 7-bit slices stay exact
   const size_t total = (size_t)padded * n_grp;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(idx % padded), grp = (int)(idx / padded);
     const int rt = r / tr, m = r % tr, ks = grp >> 1, half = grp & 1;
     const int e = ex[r];
-    uint32_t pr[ZNS][4], pi[ZNS][4];     // 8 BF16 per plane, two per word
+    uint32_t pr[NS][4], pi[NS][4];       // 8 BF16 per plane, two per word
 #pragma unroll
     for (int j = 0; j < ZG::KG; ++j) {
       const int k = ks * ZG::KSTEP + half * ZG::KG + j;
       double2 v = make_double2(0.0, 0.0);
       if (r < rows && k < it.K) v = op_elem(it, which, r, k);
-      uint32_t sr[ZNS], si[ZNS];
-      pieces<true, ZNS, true>(ldexp(v.x, -e), b, sr);
-      pieces<true, ZNS, true>(ldexp(v.y, -e), b, si);
+      uint32_t sr[NS], si[NS];
+      pieces<true, NS, true>(ldexp(v.x, -e), b, sr);
+      pieces<true, NS, true>(ldexp(v.y, -e), b, si);
 #pragma unroll
-      for (int s = 0; s < ZNS; ++s) {
+      for (int s = 0; s < NS; ++s) {
         if ((j & 1) == 0) {
           pr[s][j >> 1] = sr[s];
           pi[s][j >> 1] = si[s];
@@ -141,17 +145,19 @@ __global__ void k_zg_pack(const ZGemmItem* items, int n_items, int which, int* s
         }
       }
     }
-    unsigned char* base = out + ((size_t)rt * cp.ksteps + ks) * (2 * ZNS) * cp.plane_bytes +
+    unsigned char* base = out + ((size_t)rt * cp.ksteps + ks) * (2 * NS) * cp.plane_bytes +
                           ((size_t)half * tr + m) * 16;
 #pragma unroll
-    for (int s = 0; s < ZNS; ++s) {
+    for (int s = 0; s < NS; ++s) {
       *(uint4*)(base + (size_t)s * cp.plane_bytes) = make_uint4(pr[s][0], pr[s][1], pr[s][2], pr[s][3]);
-      *(uint4*)(base + (size_t)(ZNS + s) * cp.plane_bytes) = make_uint4(pi[s][0], pi[s][1], pi[s][2], pi[s][3]);
+      *(uint4*)(base + (size_t)(NS + s) * cp.plane_bytes) = make_uint4(pi[s][0], pi[s][1], pi[s][2], pi[s][3]);
     }
   }
 }
 
-// The GEMM: persistent, one CTA per SM over the live 128 x 64 tiles of every item.
+// The GEMM: persistent, one CTA per SM over the live 128 x 64 tiles of every item. K runs in chunks
+// of 512 (32 MMA steps): each chunk's four levels accumulate exactly enough in TMEM, and the
+// epilogue adds the chunk to C in FP64 (the first chunk writes C, or C - product for acc < 0).
 __global__ void __launch_bounds__(TC_THREADS, 1) k_zgemm(const ZGemmItem* items, int n_items, int* status) {
   constexpr uint32_t A_PLANE = TMA * ROW_BYTES, B_PLANE = TNB * ROW_BYTES;
   constexpr uint32_t A_STAGE = 2 * ZNS * A_PLANE, B_STAGE = 2 * ZNS * B_PLANE, STAGE = A_STAGE + B_STAGE;
@@ -198,7 +204,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_zgemm(const ZGemmItem* items,
   const uint32_t tmem = tmem_base_s;
   const uint32_t idesc = instr_desc(1u, TMA, TNB);
   constexpr uint32_t LBO_A = TMA * 16, LBO_B = TNB * 16, SBO = 128;
-  uint32_t g = 0;
+  uint32_t g = 0;                 // K steps processed by this CTA (stage = g % STAGES)
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     int lo = 0, hi = n_items - 1;
     while (lo < hi) {
@@ -212,116 +218,129 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_zgemm(const ZGemmItem* items,
     const int rt = (t - tile_off[lo]) / nt_b, ct = (t - tile_off[lo]) % nt_b;
     const int n_ks = cdiv(it.K, ZG::KSTEP);
     if (tid < TNB) col_exp[tid] = ((const int*)(it.TB + cb.exp_off))[ct * TNB + tid];
-    if (tid == 0) {
-      const unsigned char* gA = it.TA + (size_t)rt * ca.ksteps * A_STAGE;
-      const unsigned char* gB = it.TB + (size_t)ct * cb.ksteps * B_STAGE;
-      auto load = [&](int ks, uint32_t gg) {
-        unsigned char* st = smem + (gg % STAGES) * STAGE;
-        uint64_t* bar = &bar_full[gg % STAGES];
-        mbar_expect_tx(bar, STAGE);
-        bulk_g2s(st, gA + (size_t)ks * A_STAGE, A_STAGE, bar);
-        bulk_g2s(st + A_STAGE, gB + (size_t)ks * B_STAGE, B_STAGE, bar);
-      };
-      auto par = [](uint32_t gg) { return (gg / STAGES) & 1u; };
-      bool ok = true;
-      uint32_t loaded = g, waited = g, committed = 0;
-      bool any_commit = false;
-      bool init[NLEV] = {false, false, false, false};
-      for (int ks = 0; ks < n_ks && ks < STAGES - 1; ++ks) {
-        load(ks, g + ks);
-        loaded = g + ks + 1;
-      }
-      for (int ks = 0; ks < n_ks && ok; ++ks) {
-        const uint32_t gg = g + ks;
-        ok = mbar_wait(&bar_full[gg % STAGES], par(gg));
-        if (!ok) break;
-        waited = gg + 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const unsigned char* sa = smem + (gg % STAGES) * STAGE;
-        const unsigned char* sb = sa + A_STAGE;
-#pragma unroll
-        for (int s = 0; s < ZNS; ++s) {
-#pragma unroll
-          for (int u = 0; u < ZNS - s; ++u) {
-            const int L = (s + u) < NLEV - 1 ? (s + u) : NLEV - 1;
-            const uint32_t dre = tmem + (2 * L) * TNB, dim = dre + TNB;
-            const uint64_t ar = smem_desc(sa + s * A_PLANE, LBO_A, SBO);
-            const uint64_t ai = smem_desc(sa + (ZNS + s) * A_PLANE, LBO_A, SBO);
-            const uint64_t br = smem_desc(sb + u * B_PLANE, LBO_B, SBO);
-            const uint64_t bi = smem_desc(sb + (ZNS + u) * B_PLANE, LBO_B, SBO);
-            mma<true>(dre, ar, br, idesc, init[L]);
-            mma<true>(dre, ai, bi, idesc | NEG_A, true);
-            mma<true>(dim, ar, bi, idesc, init[L]);
-            mma<true>(dim, ai, br, idesc, true);
-            init[L] = true;
-          }
-        }
-        mma_commit(&bar_empty[gg % STAGES]);
-        committed = gg;
-        any_commit = true;
-        const int nk = ks + STAGES - 1;
-        if (nk < n_ks) {
-          if (ks >= 1) ok = mbar_wait(&bar_empty[(gg - 1) % STAGES], par(gg - 1));
-          if (!ok) break;
-          load(nk, g + nk);
-          loaded = g + nk + 1;
-        }
-      }
-      if (ok && any_commit) ok = mbar_wait(&bar_empty[committed % STAGES], par(committed));
-      if (!ok) {
-        atomicOr(status, ST_TIMEOUT);
-        abort_s = 1;
-        for (uint32_t q = waited; q < loaded; ++q) mbar_wait(&bar_full[q % STAGES], par(q));
-        if (any_commit) mbar_wait(&bar_empty[committed % STAGES], par(committed));
-      }
-    }
-    g += n_ks;
-    __syncthreads();
-    if (abort_s) break;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: thread = row m of the tile, 8 columns per TMEM load
+    const unsigned char* gA = it.TA + (size_t)rt * ca.ksteps * A_STAGE;
+    const unsigned char* gB = it.TB + (size_t)ct * cb.ksteps * B_STAGE;
     const int m = rt * TMA + warp * 32 + lane;
     const int e_m = ((const int*)(it.TA + ca.exp_off))[m];
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     bool bad = false;
-    for (int c0 = 0; c0 < TNB; c0 += 8) {
-      double re[8], im[8];
-      {
-        float x[8], y[8];
-        tmem_ld8(tmem + lane_base + c0, x);
-        tmem_ld8(tmem + lane_base + TNB + c0, y);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          re[j] = (double)x[j];
-          im[j] = (double)y[j];
+    for (int ks0 = 0; ks0 < n_ks; ks0 += ZKC_STEPS) {
+      const int nk = min(ZKC_STEPS, n_ks - ks0);
+      if (tid == 0) {
+        auto load = [&](int ks, uint32_t gg) {
+          unsigned char* st = smem + (gg % STAGES) * STAGE;
+          uint64_t* bar = &bar_full[gg % STAGES];
+          mbar_expect_tx(bar, STAGE);
+          bulk_g2s(st, gA + (size_t)(ks0 + ks) * A_STAGE, A_STAGE, bar);
+          bulk_g2s(st + A_STAGE, gB + (size_t)(ks0 + ks) * B_STAGE, B_STAGE, bar);
+        };
+        auto par = [](uint32_t gg) { return (gg / STAGES) & 1u; };
+        bool ok = true;
+        uint32_t loaded = g, waited = g, committed = 0;
+        bool any_commit = false;
+        bool init[NLEV] = {false, false, false, false};
+        // prologue: the chunk's first STAGES - 1 steps (their stages were freed by the last wait)
+        for (int ks = 0; ks < nk && ks < STAGES - 1; ++ks) {
+          load(ks, g + ks);
+          loaded = g + ks + 1;
         }
+        for (int ks = 0; ks < nk && ok; ++ks) {
+          const uint32_t gg = g + ks;
+          ok = mbar_wait(&bar_full[gg % STAGES], par(gg));
+          if (!ok) break;
+          waited = gg + 1;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const unsigned char* sa = smem + (gg % STAGES) * STAGE;
+          const unsigned char* sb = sa + A_STAGE;
 #pragma unroll
-        for (int L = 1; L < NLEV; ++L) {
-          tmem_ld8(tmem + lane_base + (2 * L) * TNB + c0, x);
-          tmem_ld8(tmem + lane_base + (2 * L + 1) * TNB + c0, y);
+          for (int s = 0; s < ZNS; ++s) {
+#pragma unroll
+            for (int u = 0; u < ZNS - s; ++u) {
+              const int L = (s + u) < NLEV - 1 ? (s + u) : NLEV - 1;
+              const uint32_t dre = tmem + (2 * L) * TNB, dim = dre + TNB;
+              const uint64_t ar = smem_desc(sa + s * A_PLANE, LBO_A, SBO);
+              const uint64_t ai = smem_desc(sa + (ZNS + s) * A_PLANE, LBO_A, SBO);
+              const uint64_t br = smem_desc(sb + u * B_PLANE, LBO_B, SBO);
+              const uint64_t bi = smem_desc(sb + (ZNS + u) * B_PLANE, LBO_B, SBO);
+              mma<true>(dre, ar, br, idesc, init[L]);
+              mma<true>(dre, ai, bi, idesc | NEG_A, true);
+              mma<true>(dim, ar, bi, idesc, init[L]);
+              mma<true>(dim, ai, br, idesc, true);
+              init[L] = true;
+            }
+          }
+          mma_commit(&bar_empty[gg % STAGES]);
+          committed = gg;
+          any_commit = true;
+          const int nx = ks + STAGES - 1;
+          if (nx < nk) {
+            if (ks >= 1) ok = mbar_wait(&bar_empty[(gg - 1) % STAGES], par(gg - 1));
+            if (!ok) break;
+            load(nx, g + nx);
+            loaded = g + nx + 1;
+          }
+        }
+        if (ok && any_commit) ok = mbar_wait(&bar_empty[committed % STAGES], par(committed));
+        if (!ok) {
+          atomicOr(status, ST_TIMEOUT);
+          abort_s = 1;
+          for (uint32_t q = waited; q < loaded; ++q) mbar_wait(&bar_full[q % STAGES], par(q));
+          if (any_commit) mbar_wait(&bar_empty[committed % STAGES], par(committed));
+        }
+      }
+      g += nk;
+      __syncthreads();
+      if (abort_s) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // epilogue of the chunk: thread = row m of the tile, 8 columns per TMEM load
+      const bool first = ks0 == 0;
+      for (int c0 = 0; c0 < TNB; c0 += 8) {
+        double re[8], im[8];
+        {
+          float x[8], y[8];
+          tmem_ld8(tmem + lane_base + c0, x);
+          tmem_ld8(tmem + lane_base + TNB + c0, y);
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            re[j] += (double)x[j];
-            im[j] += (double)y[j];
+            re[j] = (double)x[j];
+            im[j] = (double)y[j];
+          }
+#pragma unroll
+          for (int L = 1; L < NLEV; ++L) {
+            tmem_ld8(tmem + lane_base + (2 * L) * TNB + c0, x);
+            tmem_ld8(tmem + lane_base + (2 * L + 1) * TNB + c0, y);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              re[j] += (double)x[j];
+              im[j] += (double)y[j];
+            }
+          }
+        }
+        if (m < it.M) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int n = ct * TNB + c0 + j;
+            if (n >= it.N) continue;
+            const int e = e_m + col_exp[c0 + j];
+            double2 v = make_double2(ldexp(re[j], e), ldexp(im[j], e));
+            if (it.acc < 0) v = make_double2(-v.x, -v.y);
+            double2* cp = it.C + m + (size_t)n * it.ldc;
+            if (!first || it.acc < 0) {
+              const double2 o = *cp;
+              v = make_double2(o.x + v.x, o.y + v.y);
+            }
+            bad |= !(isfinite(v.x) && isfinite(v.y));
+            *cp = v;
           }
         }
       }
-      if (m < it.M) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int n = ct * TNB + c0 + j;
-          if (n >= it.N) continue;
-          const int e = e_m + col_exp[c0 + j];
-          const double2 v = make_double2(ldexp(re[j], e), ldexp(im[j], e));
-          bad |= !(isfinite(v.x) && isfinite(v.y));
-          it.C[m + (size_t)n * it.ldc] = v;
-        }
-      }
+      // TMEM reads complete before the next chunk's MMAs overwrite the accumulators
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
+    if (abort_s) break;
     if (bad && it.flag) *it.flag = 1;
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();

@@ -29,9 +29,10 @@ def engine_args_from_oracle(cis):
     return chains, mpos
 
 
-def run_gpu(w, cis, ops, K=None, precision="fp64", insert=None, use_graph=True, multiplet_tol=1e-12, route=None):
+def run_gpu(w, cis, ops, K=None, precision="fp64", insert=None, use_graph=True, multiplet_tol=None, route=None):
     import paper_2201_05529_gb300._capi as capi
     K = w.K if K is None else K
+    multiplet_tol = w.multiplet_tol if multiplet_tol is None else multiplet_tol
     chains, mpos = engine_args_from_oracle(cis)
     eng = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, precision=precision,
                       multiplet_tol=multiplet_tol, max_steps=K, use_graph=use_graph, route=route)
@@ -44,7 +45,8 @@ def run_gpu(w, cis, ops, K=None, precision="fp64", insert=None, use_graph=True, 
     return eng, obs, tr
 
 
-def run_oracle(w, cis, ops, K=None, insert=None, multiplet_tol=1e-12):
+def run_oracle(w, cis, ops, K=None, insert=None, multiplet_tol=None):
+    multiplet_tol = w.multiplet_tol if multiplet_tol is None else multiplet_tol
     res = []
     for c, ci in enumerate(cis):
         ins = None

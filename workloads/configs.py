@@ -72,6 +72,7 @@ class Workload:
     eps: float                      # relative singular-value threshold (App. A.2)
     kappa_max: int                  # PT-MPO bond cap
     eps_tempo: float = 1e-7         # PT-MPO relative SVD threshold
+    multiplet_tol: float = 1e-12    # a cut may not split singular values closer than this x s_max
     memory_steps: int = 0           # Delta K_max; 0 = every step of the run (no memory cut)
     two_time: Optional[Tuple[int, str]] = None   # (site, 'x'|'y'|'z') for <s(t) s(0)> at that site
     random_state: Optional[dict] = None          # stress workload: explicit tensors
@@ -112,7 +113,10 @@ def _config3():
     init = "".join("u" if n == N // 2 else "d" for n in range(N))
     ch = ChainSpec(N=N, eps=tuple([0.0] * N), J=tuple([(1.0, 1.0, 0.0)] * (N - 1)), init=init,
                    baths=tuple([b] * N))
+    # multiplet tolerance 1e-9: the U(1)-symmetric chain's exact multiplets (gaps ~1e-16) are kept whole
+    # by any SVD accurate to well below 1e-9 of s_max, the tensor-core fast path included
     return Workload("xy21_allbaths", (ch,), dt=0.1, K=100, chi_max=128, eps=1e-6, kappa_max=16,
+                    multiplet_tol=1e-9,
                     notes="N=21 isotropic XY, a bath on every site, one central excitation")
 
 
