@@ -152,6 +152,32 @@ def log_flops(rec):
     return tot, full
 
 
+RSVD_POWER = 2          # the fast path's power iterations (rsvd.cu)
+
+
+def hqr_flops(m, n):
+    """Complex Householder QR of an m x n matrix with the explicit Q: 8(mn^2 - n^3/3) to factor and
+    as much again to form Q (Golub-Van Loan, complex = 4 real)."""
+    return 16.0 * (m * n * n - n ** 3 / 3.0) if m >= n > 0 else 0.0
+
+
+def rsvd_flops(rec):
+    """The fast path's randomized SVD over the window from the device bond log [K, 6, nb, >=6]
+    (rows, columns, range-finder width l, ..., kept chi): the range finder's QRs ((1 + q) of the
+    m x l sketches Y, (q + 1) of the n x l sketches Z) and the tensor-core products ((1 + q) D Omega /
+    D Qz, (q + 1) D^H Q, the residual D - Q Z^H, the kept vectors Q Wr and Qb Ur; complex MAC = 8)."""
+    qr = gemm = 0.0
+    q = RSVD_POWER
+    for r in rec.reshape(-1, rec.shape[-1]):
+        mD, nD, l, chi = int(r[0]), int(r[1]), int(r[2]), int(r[5])
+        if mD <= 0 or nD <= 0 or l <= 0:
+            continue
+        m, n = max(mD, nD), min(mD, nD)
+        qr += (1 + q) * hqr_flops(m, l) + (q + 1) * hqr_flops(n, l)
+        gemm += 8.0 * m * n * l * ((1 + q) + (q + 1) + 1) + 8.0 * (m + n) * l * chi
+    return qr, gemm
+
+
 def bond_sizes(chis, kaps, N):
     """(m_L, n_L, m_R, n_R, r_L, r_R, chi) of every bond for the given dims (App. A.2)."""
     out = []
@@ -304,7 +330,6 @@ def run_ours(args, rank, world, local):
     blog, disc = eng.read_bond_log(W, K)
     dims = [eng.get_dims(c) for c in range(n_chains)]
     eng.destroy()
-    fl_svd, fl_svd_full = log_flops(blog)
     fl_rest = fl_theta = 0.0
     for c, (chi, kap) in enumerate(dims):
         o_, t_ = step_flops_rest(list(chi), list(kap), chains[c]["N"])
@@ -323,13 +348,35 @@ def run_ours(args, rank, world, local):
 
     # --- the plain FP64 GPU path on the same window (FP32-TC vs FP64)
     fp64 = None
+    fp64_svd = None
     if args.precision != "fp64" and not args.no_fp64_path:
         e64 = make("fp64")
         e64.step(W)
         e64.sync()
         ms64 = _timed_window(e64, K, stream, flush, torch)
         hist64, _ = e64.read_history(W, K + 1)
+        blog64, _ = e64.read_bond_log(W, K)
         e64.destroy()
+        # its SVD's roofline on a short stage-timed sub-window (a second engine at step W)
+        Ks = min(K, 5)
+        e64s = make("fp64", graph=False)
+        e64s.step(W)
+        e64s.sync()
+        e64s.set_timing(True)
+        st64 = np.zeros(9)
+        for i in range(Ks):
+            flush.fill_(float(i))
+            e64s.step(1)
+            st64 += e64s.get_timing()
+        e64s.destroy()
+        f64, _ = log_flops(blog64[:Ks])
+        ms64_svd = (st64[3] + st64[7] + st64[8]) / (Ks * 6)
+        ach64 = (f64 / (Ks * 6)) / (ms64_svd / 1e3) / 1e12
+        fp64_peak_ = SM_COUNT * FP64_FLOPS_PER_CLK_PER_SM * 2070.0 * 1e6 / 1e12
+        fp64_svd = {"kernel": "FP64 path's bond SVD (pivoted QR, Jacobi sweeps on R^H, U = D V)", "bound": "alu",
+                    "achieved": ach64, "peak": fp64_peak_, "unit": "TFLOP/s", "frac": ach64 / fp64_peak_,
+                    "window": f"steps {W}..{W + Ks}", "ms_per_launch": ms64_svd,
+                    "work": "Golub-Van Loan counts with the pivoted QR's rank (bond log)"}
         d = np.abs(hist64 - hist_fast)
         fp64 = {"value": site_steps_per_step * K / (float(np.sum(ms64)) / 1e3),
                 "ms_per_step": float(np.mean(ms64)), "steps": K,
@@ -337,40 +384,69 @@ def run_ours(args, rank, world, local):
                 "max_sz_diff_vs_fast_path": float(np.max(d)),
                 "max_sz_diff_per_step": [float(x) for x in d.max(axis=(1, 2, 3))]}
 
-    # --- roofline of the dominant stage: the bond SVD (pivoted QR, Jacobi sweeps, U = D V)
+    # --- roofline of the dominant kernel
     n_layers = 6
-    svd_ms = stage[3] + stage[7] + stage[8]
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp64_peak = SM_COUNT * FP64_FLOPS_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
-    achieved = (fl_svd / (K * n_layers)) / (svd_ms / K / n_layers / 1e3) / 1e12
-    traffic, tsrc = traffic_record(["qrcp.cu", "jacobi_grid.cu", "svd_gemm.cu"])
     mp = measured_peaks()
     src = ("MEASURED_PEAKS.json gives HBM copy and bf16 GEMM peaks only" if mp else "MEASURED_PEAKS.json absent")
+    peak_src = ("derived: 152 SMs x 4 FP64 flop/clk x median SM clock (of derived; " + src +
+                "; a DFMA probe measured 1.20 TFLOP/s)")
+    bf16 = float(mp["bf16_tflops"]) if mp and "bf16_tflops" in mp else 1900.0
     sweeps = blog[..., 3]
-    roofline = {"bound": "alu", "kernel": "bond SVD, one launch chain per layer: pivoted QR stopping at D's noise "
-                                          "level (k_qrcp_cl / k_qrcp_grid), FP64 one-sided Jacobi sweeps on "
-                                          "B = R^H (k_jacobi_grid), U = D V (k_mix_gemm)",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                "traffic": traffic, "traffic_source": tsrc,
-                "work": "Golub-Van Loan counts of the SVD of each m x n D of numerical rank k (the pivoted QR's "
-                        "rank, read from the device bond log): QR to rank k + SVD of the n x k factor + U = D V",
-                "work_tflop_window": fl_svd / 1e12,
-                "work_full_rank_tflop_window": fl_svd_full / 1e12,
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x median SM clock (of derived; "
-                               + src + "; a DFMA probe measured 1.20 TFLOP/s)",
-                "svd_ms_per_launch": svd_ms / K / n_layers,
-                "fp64_sweeps_mean": float(np.mean(sweeps[sweeps > 0])) if np.any(sweeps > 0) else 0.0,
-                "fp32_sweeps_mean": float(np.mean(blog[..., 4][blog[..., 4] > 0])) if np.any(blog[..., 4] > 0) else 0.0,
-                "rank_over_n_mean": float(np.mean((blog[..., 2] / np.maximum(1, np.minimum(blog[..., 0], blog[..., 1])))
-                                                  [blog[..., 0] > 0])),
-                "stage_ms_per_step": {"site": stage[0] / K, "blocks_qr": stage[1] / K, "theta": stage[2] / K,
-                                      "svd_fp64_sweeps": stage[3] / K, "svd_fp32_sweeps": stage[7] / K,
-                                      "svd_precond": stage[8] / K, "truncate": stage[4] / K,
-                                      "recover": stage[5] / K, "readout": stage[6] / K}}
+    stage_ms = {"site": stage[0] / K, "blocks_qr": stage[1] / K, "theta": stage[2] / K,
+                "svd_jacobi_sweeps": stage[3] / K, "svd_range_finder_qr": stage[7] / K,
+                "svd_products_or_precond": stage[8] / K, "truncate": stage[4] / K,
+                "recover": stage[5] / K, "readout": stage[6] / K}
+    if args.precision == "bf16_ozaki":
+        fl_qr, fl_gemm = rsvd_flops(blog)
+        fl_path = fl_qr + fl_gemm
+        n_qr = (1 + RSVD_POWER) + (RSVD_POWER + 1)          # QR launches per layer
+        qr_ms = stage[7] / K / n_layers / n_qr              # per launch
+        achieved = (fl_qr / (K * n_layers * n_qr)) / (qr_ms / 1e3) / 1e12
+        traffic, tsrc = traffic_record(["hqr_grid.cu"])
+        roofline = {"bound": "alu", "kernel": "k_hqr_items: whole-GPU Householder QR (explicit Q) of the randomized "
+                                              "range finder's sketches Y (m x l) and Z (n x l) of every bond of a layer",
+                    "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                    "traffic": traffic, "traffic_source": tsrc,
+                    "work": "16 (m l^2 - l^3 / 3) per m x l QR with its explicit Q (GVL, complex = 4 real), "
+                            f"{n_qr} QRs per bond update, m, n, l read from the device bond log",
+                    "work_tflop_window": fl_qr / 1e12, "peak_source": peak_src,
+                    "ms_per_launch": qr_ms, "launches_per_layer": n_qr,
+                    "jacobi_sweeps_mean": float(np.mean(sweeps[sweeps > 0])) if np.any(sweeps > 0) else 0.0,
+                    "range_width_over_n_mean": float(np.mean((blog[..., 2] / np.maximum(1, np.minimum(blog[..., 0], blog[..., 1])))
+                                                             [blog[..., 0] > 0])),
+                    "stage_ms_per_step": stage_ms}
+        # the sliced tensor-core products (the fast path's dense contractions)
+        gemm_s = stage[8] / 1e3
+        roofline["tensor_products"] = {
+            "kernel": "k_zgemm (+ k_zg_rowexp / k_zg_pack): D Omega, D^H Q, D Qz, D - Q Z^H, Q Wr, Qb Ur",
+            "bound": "tensor", "achieved": fl_gemm / gemm_s / 1e12, "peak": bf16, "unit": "TFLOP/s",
+            "frac": fl_gemm / gemm_s / 1e12 / bf16,
+            "achieved_executed_bf16": 21.0 * fl_gemm / gemm_s / 1e12,
+            "work": "complex products at 8 flops per MAC (algorithmic); each runs as 21 slice-pair x 4 real "
+                    "BF16 products, the executed rate is 21 x the algorithmic one; stage time includes the "
+                    "packing passes and the plan kernels",
+            "peak_source": "of measured bf16 GEMM burst"}
+    else:
+        fl_svd, fl_svd_full = log_flops(blog)
+        fl_path = fl_svd
+        svd_ms = stage[3] + stage[7] + stage[8]
+        achieved = (fl_svd / (K * n_layers)) / (svd_ms / K / n_layers / 1e3) / 1e12
+        traffic, tsrc = traffic_record(["qrcp.cu", "jacobi_grid.cu", "svd_gemm.cu"])
+        roofline = {"bound": "alu", "kernel": "FP64 bond SVD, one launch chain per layer: pivoted QR stopping at "
+                                              "D's noise level, one-sided Jacobi sweeps on B = R^H, U = D V",
+                    "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                    "traffic": traffic, "traffic_source": tsrc,
+                    "work": "Golub-Van Loan counts of the SVD of each m x n D of numerical rank k (the pivoted "
+                            "QR's rank, read from the device bond log): QR to rank k + SVD of the n x k factor + U = D V",
+                    "work_tflop_window": fl_svd / 1e12, "work_full_rank_tflop_window": fl_svd_full / 1e12,
+                    "peak_source": peak_src, "ms_per_launch": svd_ms / K / n_layers,
+                    "jacobi_sweeps_mean": float(np.mean(sweeps[sweeps > 0])) if np.any(sweeps > 0) else 0.0,
+                    "stage_ms_per_step": stage_ms}
     if args.precision != "fp64" and stage[2] > 0:
-        # theta + gate on the tensor cores (the dense contraction of the fast path)
-        bf16 = float(mp["bf16_tflops"]) if mp and "bf16_tflops" in mp else 1900.0
+        # theta + gate on the tensor cores
         tpeak = bf16 * (1.1 / 2.25) if args.precision in ("tf32x3", "tf32x1") else bf16
         tach = (fl_theta / K) / (stage[2] / K / 1e3) / 1e12
         roofline["theta_tensor"] = {
@@ -378,6 +454,8 @@ def run_ours(args, rank, world, local):
             "achieved": tach, "peak": tpeak, "unit": "TFLOP/s", "frac": tach / tpeak,
             "work": "128 r^2 chi + 2048 r^2 per bond update (algorithmic, complex MAC = 8)",
             "peak_source": "of measured bf16 GEMM burst" + (" x 1.1/2.25" if "tf32" in args.precision else "")}
+    if fp64_svd is not None:
+        roofline["fp64_path_svd"] = fp64_svd
 
     # --- end to end through the C ABI: host inputs -> init (H2D) -> W + K steps -> history (D2H);
     # the work counted is the K-step window's only, while the timed region also holds the init and
@@ -412,7 +490,7 @@ def run_ours(args, rank, world, local):
            "clocks": clocks, "roofline": roofline, "e2e": e2e,
            "gpu_launches": int(launches_per_step) * K,
            "gpu_launches_per_step": int(launches_per_step),
-           "algorithmic_tflops": (fl_svd + fl_rest) / (total_ms / 1e3) / 1e12,
+           "algorithmic_tflops": (fl_path + fl_rest) / (total_ms / 1e3) / 1e12,
            "max_discarded_weight": float(np.max(disc)) if disc.size else 0.0}
     if fp64 is not None:
         out["fp64_path"] = fp64

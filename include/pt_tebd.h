@@ -192,10 +192,11 @@ int pt_tebd_destroy(pt_tebd_t h);
 const char* pt_tebd_last_error(pt_tebd_t h);   /* h may be NULL: last global error */
 
 /* Per-stage device time of the last pt_tebd_step call with timing enabled, in milliseconds:
- * [0] site contraction, [1] block build + QR, [2] theta + gate, [3] SVD (FP64 sweeps),
- * [4] truncation, [5] Gamma recovery, [6] readout, [7] SVD FP32 sweeps (fast path),
- * [8] SVD preconditioning: pivoted QR and the U = D V / sigma finish, or the mixed path's FP64
- * re-orthonormalisation. Timing mode launches eagerly (no graph). */
+ * [0] site contraction, [1] block build + outer-block QR, [2] theta + gate, [3] SVD Jacobi sweeps,
+ * [4] truncation, [5] Gamma recovery, [6] readout, [7] the fast path's range-finder Householder
+ * QRs, [8] FP64 path: pivoted QR and the U = D V / sigma finish; fast path: the tensor-core
+ * products of the randomized SVD (sketches, projection, residual, kept vectors). Timing mode
+ * launches eagerly (no graph). */
 int pt_tebd_set_timing(pt_tebd_t h, int enable);
 int pt_tebd_get_timing(pt_tebd_t h, double* ms9);
 
@@ -209,6 +210,15 @@ int pt_tebd_get_timing(pt_tebd_t h, double* ms9);
 size_t pt_svd_scratch_bytes(int m, int n, int batch);
 int pt_svd_f64(const double* A, int m, int n, int batch, double* sigma, double* U, double* V,
                void* scratch, int max_sweeps, void* cuda_stream);
+
+/* Batched FP64 Householder QR with the explicit Q (the whole-GPU kernel of the outer-block
+ * reductions, App. A.2 (d-e), and of the fast path's range finder): A_b (m x n complex,
+ * column-major, 1 <= n <= m, b < batch, contiguous) is replaced by Q_b (m x n, orthonormal columns),
+ * R_b (n x n, column-major, upper triangular) is written, A_b(in) = Q_b R_b. scratch: device workspace
+ * of pt_qr_scratch_bytes(m, n, batch) bytes. Synchronous. Errors: PT_ERR_ARG, PT_ERR_CAPACITY
+ * (n x batch above the kernel's column capacity), PT_ERR_DEVICE_TIMEOUT (a bounded barrier wait). */
+size_t pt_qr_scratch_bytes(int m, int n, int batch);
+int pt_qr_f64(double* A, int m, int n, int batch, double* R, void* scratch, void* cuda_stream);
 
 /* Batched complex GEMM of the fast path on the tensor cores (the products of the fast path's bond
  * SVD, App. A.2 (f)): C_b = opA(A_b) opB(B_b), b < batch, C_b m x n, inner dimension k. Every

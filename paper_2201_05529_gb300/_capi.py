@@ -29,7 +29,7 @@ EXPORTS = [
     "pt_tune_cache_lookup", "pt_tune_cache_store",
     "pt_tebd_sync", "pt_tebd_destroy", "pt_tebd_last_error", "pt_tebd_set_timing",
     "pt_tebd_get_timing", "pt_svd_scratch_bytes", "pt_svd_f64", "pt_svd_f64_noalloc",
-    "pt_zgemm_scratch_bytes", "pt_zgemm_sliced", "pt_selftest_grid_barrier",
+    "pt_zgemm_scratch_bytes", "pt_zgemm_sliced", "pt_qr_scratch_bytes", "pt_qr_f64", "pt_selftest_grid_barrier",
 ]
 
 
@@ -115,6 +115,9 @@ lib.pt_zgemm_scratch_bytes.restype = C.c_size_t
 lib.pt_zgemm_sliced.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_longlong,
                                 C.c_void_p, C.c_int, C.c_longlong, C.c_void_p, C.c_int, C.c_longlong, C.c_int,
                                 C.c_void_p, C.c_void_p]
+lib.pt_qr_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
+lib.pt_qr_scratch_bytes.restype = C.c_size_t
+lib.pt_qr_f64.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
 lib.pt_svd_f64_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_int, C.c_void_p]
 NOALLOC_MAX_BYTES = 16 << 20     # PT_SVD_NOALLOC_MAX_BYTES
@@ -390,6 +393,19 @@ def zgemm_sliced(opA, opB, A, B, C_out, m, n, k, scratch, stream=None):
                              C.c_void_p(C_out.data_ptr()), ldc, C_out.shape[1] * C_out.shape[2], int(b),
                              C.c_void_p(scratch.data_ptr()), st)
     _check(rc, None)
+
+
+def qr_scratch_bytes(m, n, batch):
+    return int(lib.pt_qr_scratch_bytes(int(m), int(n), int(batch)))
+
+
+def qr_f64(A, R, scratch, stream=None):
+    """pt_qr_f64 on device tensors: A [batch, n, m] complex128 (each entry column-major m x n) is
+    replaced by Q; R [batch, n, n] (column-major) receives the triangular factor."""
+    b, n, m = A.shape
+    st = stream if stream is not None else current_stream_handle()
+    _check(lib.pt_qr_f64(C.c_void_p(A.data_ptr()), int(m), int(n), int(b), C.c_void_p(R.data_ptr()),
+                         C.c_void_p(scratch.data_ptr()), st), None)
 
 
 def svd_f64_noalloc(A, sigma, U, V, max_sweeps=0, stream=None):

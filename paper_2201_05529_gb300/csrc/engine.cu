@@ -267,10 +267,36 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n, int layer) {
   if (h->use_rsvd) {
     // fast path: randomized truncated SVD (tensor-core products, whole-GPU QR and l x l Jacobi)
     const ptk::RsvdLists& L = work == h->d_odd ? h->rs_odd : h->rs_even;
+    const int mc = L.m_cap, lc = L.l_cap;
+    int* st = h->T.status;
+    // timing categories: 8 the tensor-core products, 7 the Householder QRs of the range finder
+    auto gemm = [&](const ptk::ZGemmItem* it, int ncap) {
+      ev_begin(h, 8, &e);
+      ptk::launch_zgemm(it, n, L.tile_cap, mc, ncap, st, s);
+      ev_end(h, e);
+    };
+    auto qr = [&](const ptk::QRItem* it) {
+      ev_begin(h, 7, &e);
+      ptk::launch_hqr_items(it, n, h->grid_blocks, h->d_sync3, st, s);
+      ev_end(h, e);
+    };
     ev_begin(h, 8, &e);
-    ptk::launch_rsvd(h->T, work, n, L, h->opt.chi_max, ptk::RSVD_OVERSAMPLE, h->d_omega, h->ld_omega,
-                     h->grid_blocks, h->d_sync3, s);
+    ptk::launch_rsvd_plan(h->T, work, n, L, h->opt.chi_max, ptk::RSVD_OVERSAMPLE, h->d_omega, h->ld_omega, s);
     ev_end(h, e);
+    gemm(L.gy1, lc);                                    // Y = D Omega
+    qr(L.q1);
+    for (int it = 0; it < ptk::RSVD_POWER; ++it) {
+      gemm(L.gz1, lc);                                  // Z = D^H Q
+      qr(L.qz);
+      gemm(L.gy2, lc);                                  // Y = D Qz
+      qr(L.q2);
+    }
+    gemm(L.gz2, lc);                                    // Z = D^H Q = B^H
+    gemm(L.gres, mc);                                   // D - Q Z^H
+    ev_begin(h, 8, &e);
+    ptk::launch_rsvd_tail_norm(work, n, s);
+    ev_end(h, e);
+    qr(L.qb);                                           // Z = Qb Rb
     ev_begin(h, 3, &e);
     const double tol_scale = 9.007199254740992e6;     // |cos| <= 1e-9, below the products' accuracy
     ptk::launch_jacobi_grid(work, n, h->grid_blocks, h->opt.max_sweeps, h->d_sync3, cnt, h->T.status, s, 1, 1,
@@ -1497,6 +1523,74 @@ size_t pt_svd_scratch_bytes(int m, int n, int batch) {
   if (m < 1 || n < 1 || batch < 1) return 0;
   size_t offs[8];
   return svd_layout(m, n, batch, offs);
+}
+
+static size_t hqr_layout(int m, int n, int batch, size_t* offs) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o += (bytes + 255) & ~size_t(255);
+    return r;
+  };
+  offs[0] = take(sizeof(ptk::QRItem) * (size_t)batch);
+  offs[1] = take(sizeof(double2) * (size_t)m * n * batch);     // reflectors
+  offs[2] = take(sizeof(double) * (size_t)n * batch);          // tau
+  offs[3] = take(sizeof(unsigned) * 4);                        // grid barrier
+  offs[4] = take(sizeof(int));                                 // status
+  return o;
+}
+
+size_t pt_qr_scratch_bytes(int m, int n, int batch) {
+  if (m < 1 || n < 1 || n > m || batch < 1) return 0;
+  size_t offs[5];
+  return hqr_layout(m, n, batch, offs);
+}
+
+int pt_qr_f64(double* A, int m, int n, int batch, double* R, void* scratch, void* cuda_stream) {
+  if (!A || !R || !scratch || m < 1 || n < 1 || n > m || batch < 1 || batch > 2048) {
+    g_err = "pt_qr_f64: bad arguments (need 1 <= n <= m, 1 <= batch <= 2048)";
+    return PT_ERR_ARG;
+  }
+  const int blocks = ptk::jacobi_grid_blocks();
+  if (blocks <= 0 || !ptk::hqr_items_ok()) {
+    g_err = "pt_qr_f64: the device cannot co-schedule the whole-GPU kernel";
+    return PT_ERR_CUDA;
+  }
+  if ((long long)n * batch > (long long)blocks * 384) {
+    g_err = "pt_qr_f64: n x batch exceeds the kernel's column capacity";
+    return PT_ERR_CAPACITY;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  size_t offs[5];
+  hqr_layout(m, n, batch, offs);
+  char* base = (char*)scratch;
+  ptk::QRItem* items = (ptk::QRItem*)(base + offs[0]);
+  unsigned* sync3 = (unsigned*)(base + offs[3]);
+  int* status = (int*)(base + offs[4]);
+  std::vector<ptk::QRItem> h(batch);
+  for (int b = 0; b < batch; ++b)
+    h[b] = ptk::QRItem{(double2*)A + (size_t)b * m * n, (double2*)(base + offs[1]) + (size_t)b * m * n,
+                       (double2*)R + (size_t)b * n * n, (double*)(base + offs[2]) + (size_t)b * n, m, n};
+  cudaMemcpyAsync(items, h.data(), sizeof(ptk::QRItem) * batch, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(status, 0, sizeof(int), st);
+  ptk::launch_hqr_items(items, batch, blocks, sync3, status, st);
+  int hs = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    g_err = std::string("pt_qr_f64: ") + cudaGetErrorString(e);
+    return PT_ERR_CUDA;
+  }
+  if (hs & ST_TIMEOUT) {
+    g_err = "pt_qr_f64: a grid barrier wait ran out of time";
+    return PT_ERR_DEVICE_TIMEOUT;
+  }
+  if (hs & ST_CAPACITY) {
+    g_err = "pt_qr_f64: capacity";
+    return PT_ERR_CAPACITY;
+  }
+  return PT_OK;
 }
 
 static size_t zgemm_layout(int m, int n, int k, int batch, size_t* offs) {

@@ -12,8 +12,9 @@
 // Q = P_0 ... P_{n-1} [I; 0]: column k needs only the stored reflectors 0..k, so that phase runs
 // without barriers.
 //
-// Reflectors as in k_householder: P_j = I - tau_j u_j u_j^H with u_j[j] = 1 (stored in HH), tau_j in
-// aux (B_L) or sig (B_R^H), the diagonal of R = beta_j. Every grid barrier wait is bounded.
+// Reflectors P_j = I - tau_j u_j u_j^H with u_j[j] = 1: the column x it was formed from is kept raw
+// in HH (rows > j) and the scale 1 / u_jj in HH[j, j]; tau_j in aux (B_L) or sig (B_R^H), the
+// diagonal of R = beta_j. Every grid barrier wait is bounded.
 #include "grid_sync.cuh"
 #include "kernels.h"
 
@@ -49,106 +50,130 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Reflector storage: P_j = I - tau_j u_j u_j^H with u_j[j] = 1 and u_j[r] = x_r s_j for r > j,
+// where x is column j as it stood when the reflector was formed (kept raw in H[:, j], rows > j) and
+// s_j = 1 / (alpha - beta) is kept in H[j, j] (the slot of the implicit unit entry); so forming a
+// reflector needs no pass of its own over the column.
+
 // y <- P_j y on rows j.. (one warp). Four rows per lane per iteration: four independent L2 loads
-// in flight per lane (the loops are latency-bound, not bandwidth-bound)
-__device__ __forceinline__ void apply_reflector(const HMat& M, int j, double2* y, int lane) {
+// in flight per lane (the loops are latency-bound, not bandwidth-bound). With NORM, also return
+// ||y_new[j+1..]||^2 and alpha = y_new[j+1], and copy y_new[j+2..] raw into H[:, j+1] (the next
+// reflector's column).
+template <bool NORM>
+__device__ __forceinline__ void apply_reflector(const HMat& M, int j, double2* y, int lane, double* nrm2_out = nullptr,
+                                                double2* alpha_out = nullptr) {
   const double t = __ldcg(M.tau + j);
-  if (t == 0.0) return;
-  const double2* u = M.H + (size_t)j * M.m;
+  if (t == 0.0 && !NORM) return;
+  const double2* x = M.H + (size_t)j * M.m;
+  const double2 sj = __ldcg(x + j);
+  double2* hn = M.H + (size_t)(j + 1) * M.m;
+  // rows j+1 .. m-1 in blocks of 128 (lane + 32 q, q < 4); the block count is the same for every
+  // lane, the last block's rows are predicated: no lane-dependent loop bounds
+  const int r0 = j + 1 + lane;
+  const int nblk = (M.m - (j + 1) + 127) >> 7;
+  // pass 1: conj(x) . y over rows > j
   double sr0 = 0.0, si0 = 0.0, sr1 = 0.0, si1 = 0.0;
-  int r = j + lane;
-  for (; r + 96 < M.m; r += 128) {
-    const double2 a0 = __ldcg(u + r), b0 = __ldcg(y + r);
-    const double2 a1 = __ldcg(u + r + 32), b1 = __ldcg(y + r + 32);
-    const double2 a2 = __ldcg(u + r + 64), b2 = __ldcg(y + r + 64);
-    const double2 a3 = __ldcg(u + r + 96), b3 = __ldcg(y + r + 96);
-    sr0 = fma(a0.x, b0.x, fma(a0.y, b0.y, sr0));              // conj(u) y
-    si0 = fma(a0.x, b0.y, fma(-a0.y, b0.x, si0));
-    sr1 = fma(a1.x, b1.x, fma(a1.y, b1.y, sr1));
-    si1 = fma(a1.x, b1.y, fma(-a1.y, b1.x, si1));
-    sr0 = fma(a2.x, b2.x, fma(a2.y, b2.y, sr0));
-    si0 = fma(a2.x, b2.y, fma(-a2.y, b2.x, si0));
-    sr1 = fma(a3.x, b3.x, fma(a3.y, b3.y, sr1));
-    si1 = fma(a3.x, b3.y, fma(-a3.y, b3.x, si1));
+  if (t != 0.0) {
+    for (int i = 0; i < nblk; ++i) {
+      const int r = r0 + (i << 7);
+      double2 a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool in = r + 32 * q < M.m;
+        a[q] = in ? __ldcg(x + r + 32 * q) : make_double2(0.0, 0.0);
+        b[q] = in ? __ldcg(y + r + 32 * q) : make_double2(0.0, 0.0);
+      }
+      sr0 = fma(a[0].x, b[0].x, fma(a[0].y, b[0].y, sr0));
+      si0 = fma(a[0].x, b[0].y, fma(-a[0].y, b[0].x, si0));
+      sr1 = fma(a[1].x, b[1].x, fma(a[1].y, b[1].y, sr1));
+      si1 = fma(a[1].x, b[1].y, fma(-a[1].y, b[1].x, si1));
+      sr0 = fma(a[2].x, b[2].x, fma(a[2].y, b[2].y, sr0));
+      si0 = fma(a[2].x, b[2].y, fma(-a[2].y, b[2].x, si0));
+      sr1 = fma(a[3].x, b[3].x, fma(a[3].y, b[3].y, sr1));
+      si1 = fma(a[3].x, b[3].y, fma(-a[3].y, b[3].x, si1));
+    }
   }
-  for (; r < M.m; r += 32) {
-    const double2 a = __ldcg(u + r), b = __ldcg(y + r);
-    sr0 = fma(a.x, b.x, fma(a.y, b.y, sr0));
-    si0 = fma(a.x, b.y, fma(-a.y, b.x, si0));
-  }
-  const double sr = warp_sum(sr0 + sr1) * t;
-  const double si = warp_sum(si0 + si1) * t;
-  r = j + lane;
-  for (; r + 96 < M.m; r += 128) {
+  const double dr = warp_sum(sr0 + sr1), di = warp_sum(si0 + si1);
+  // u^H y = y_j + conj(s) (x^H y)_{r > j};  c = tau u^H y;  y_j -= c, y_r -= x_r (s c)
+  const double2 yj = __ldcg(y + j);
+  const double2 d = make_double2(yj.x + sj.x * dr + sj.y * di, yj.y + sj.x * di - sj.y * dr);
+  const double2 c = make_double2(t * d.x, t * d.y);
+  const double2 sc = make_double2(sj.x * c.x - sj.y * c.y, sj.x * c.y + sj.y * c.x);
+  __syncwarp();
+  if (lane == 0 && t != 0.0) __stcg(y + j, make_double2(yj.x - c.x, yj.y - c.y));
+  double n0 = 0.0, n1 = 0.0;
+  double2 alpha = make_double2(0.0, 0.0);
+  for (int i = 0; i < nblk; ++i) {
+    const int r = r0 + (i << 7);
     double2 a[4], b[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      a[q] = __ldcg(u + r + 32 * q);
-      b[q] = __ldcg(y + r + 32 * q);
+      const bool in = r + 32 * q < M.m;
+      a[q] = in ? __ldcg(x + r + 32 * q) : make_double2(0.0, 0.0);
+      b[q] = in ? __ldcg(y + r + 32 * q) : make_double2(0.0, 0.0);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      b[q].x -= a[q].x * sr - a[q].y * si;
-      b[q].y -= a[q].x * si + a[q].y * sr;
-      __stcg(y + r + 32 * q, b[q]);
+      const int rr = r + 32 * q;
+      if (rr >= M.m) continue;
+      if (t != 0.0) {
+        b[q].x -= a[q].x * sc.x - a[q].y * sc.y;
+        b[q].y -= a[q].x * sc.y + a[q].y * sc.x;
+        __stcg(y + rr, b[q]);
+      }
+      if (NORM) {
+        if (rr == j + 1) alpha = b[q];
+        else __stcg(hn + rr, b[q]);
+        if (q & 1) n1 = fma(b[q].x, b[q].x, fma(b[q].y, b[q].y, n1));
+        else n0 = fma(b[q].x, b[q].x, fma(b[q].y, b[q].y, n0));
+      }
     }
   }
-  for (; r < M.m; r += 32) {
-    const double2 a = __ldcg(u + r);
-    double2 b = __ldcg(y + r);
-    b.x -= a.x * sr - a.y * si;
-    b.y -= a.x * si + a.y * sr;
-    __stcg(y + r, b);
+  if (NORM) {
+    *nrm2_out = warp_sum(n0 + n1);
+    // row j + 1 is lane 0's first row
+    alpha.x = __shfl_sync(0xffffffffu, alpha.x, 0);
+    alpha.y = __shfl_sync(0xffffffffu, alpha.y, 0);
+    *alpha_out = alpha;
   }
   __syncwarp();
 }
 
-// reflector j from column j of A (rows j..), one warp
-__device__ __forceinline__ void make_reflector(const HMat& M, int j, int lane) {
-  const double2* x = M.A + (size_t)j * M.m;
-  double p0 = 0.0, p1 = 0.0;
-  int r = j + lane;
-  for (; r + 96 < M.m; r += 128) {
-    const double2 v0 = __ldcg(x + r), v1 = __ldcg(x + r + 32), v2 = __ldcg(x + r + 64), v3 = __ldcg(x + r + 96);
-    p0 = fma(v0.x, v0.x, fma(v0.y, v0.y, p0));
-    p1 = fma(v1.x, v1.x, fma(v1.y, v1.y, p1));
-    p0 = fma(v2.x, v2.x, fma(v2.y, v2.y, p0));
-    p1 = fma(v3.x, v3.x, fma(v3.y, v3.y, p1));
-  }
-  for (; r < M.m; r += 32) {
-    const double2 v = __ldcg(x + r);
-    p0 = fma(v.x, v.x, fma(v.y, v.y, p0));
-  }
-  const double nrm2 = warp_sum(p0 + p1);
-  const double2 alpha = __ldcg(x + j);
-  const double aabs = sqrt(alpha.x * alpha.x + alpha.y * alpha.y);
-  const double nrm = sqrt(nrm2);
-  double t = 0.0;
-  double2 uj = make_double2(1.0, 0.0), beta = alpha;
-  if (nrm > 0.0) {
-    const double2 ph = aabs > 0.0 ? make_double2(alpha.x / aabs, alpha.y / aabs) : make_double2(1.0, 0.0);
-    beta = make_double2(-ph.x * nrm, -ph.y * nrm);
-    uj = make_double2(ph.x * (aabs + nrm), ph.y * (aabs + nrm));      // u_j = alpha - beta
-    const double uj2 = uj.x * uj.x + uj.y * uj.y;
-    t = 2.0 * uj2 / (nrm2 - aabs * aabs + uj2);
-  }
-  const double inv = 1.0 / (uj.x * uj.x + uj.y * uj.y);
-  const double2 ujinv = make_double2(uj.x * inv, -uj.y * inv);        // 1 / u_j
-  double2* u = M.H + (size_t)j * M.m;
-  for (r = j + lane; r < M.m; r += 32) {
-    double2 v = make_double2(1.0, 0.0);
-    if (r != j) {
-      const double2 xr = __ldcg(x + r);
-      v = nrm > 0.0 ? make_double2(xr.x * ujinv.x - xr.y * ujinv.y, xr.x * ujinv.y + xr.y * ujinv.x)
-                    : make_double2(0.0, 0.0);
-    }
-    __stcg(u + r, v);
-  }
+// reflector j from the squared norm of column j (rows j..) and its entry alpha = x_j: tau_j, the
+// scale s_j into H[j, j], beta into the diagonal of R (H[:, j] rows > j already hold x raw)
+__device__ __forceinline__ void finish_reflector(const HMat& M, int j, double nrm2, double2 alpha, int lane) {
   if (lane == 0) {
+    const double aabs = sqrt(alpha.x * alpha.x + alpha.y * alpha.y);
+    const double nrm = sqrt(nrm2);
+    double t = 0.0;
+    double2 s = make_double2(0.0, 0.0), beta = alpha;
+    if (nrm > 0.0) {
+      const double2 ph = aabs > 0.0 ? make_double2(alpha.x / aabs, alpha.y / aabs) : make_double2(1.0, 0.0);
+      beta = make_double2(-ph.x * nrm, -ph.y * nrm);
+      const double2 uj = make_double2(ph.x * (aabs + nrm), ph.y * (aabs + nrm));      // alpha - beta
+      const double uj2 = uj.x * uj.x + uj.y * uj.y;
+      t = 2.0 * uj2 / (nrm2 - aabs * aabs + uj2);
+      s = make_double2(uj.x / uj2, -uj.y / uj2);                                    // 1 / (alpha - beta)
+    }
     __stcg(M.tau + j, t);
+    __stcg(M.H + j + (size_t)j * M.m, s);
     M.R[j + (size_t)j * M.n] = beta;
   }
   __syncwarp();
+}
+
+// reflector 0 straight from column 0: one pass (norm, raw copy into H)
+__device__ __forceinline__ void first_reflector(const HMat& M, int lane) {
+  const double2* x = M.A;
+  double n0 = 0.0;
+  for (int r = 1 + lane; r < M.m; r += 32) {
+    const double2 v = __ldcg(x + r);
+    __stcg(M.H + r, v);
+    n0 = fma(v.x, v.x, fma(v.y, v.y, n0));
+  }
+  const double2 a0 = __ldcg(x);
+  const double nrm2 = warp_sum(n0) + a0.x * a0.x + a0.y * a0.y;
+  finish_reflector(M, 0, nrm2, a0, lane);
 }
 
 }  // namespace
@@ -195,16 +220,23 @@ __device__ __forceinline__ void hqr_body(const Get& get, int n_items, GridSync g
   const int cnt = s_cnt, maxn = s_maxn;
   // reflector 0 of every block
   for (int t = wid; t < cnt; t += HQ_WARPS)
-    if (s_col[t] == 0) make_reflector(s_mat[t], 0, lane);
+    if (s_col[t] == 0) first_reflector(s_mat[t], lane);
   if (!grid_barrier(gs, status)) return;
-  // step j: reflector j on columns k > j; the owner of column j + 1 forms reflector j + 1
+  // step j: reflector j on columns k > j; the owner of column j + 1 forms reflector j + 1 from the
+  // same pass (its norm and raw copy)
   for (int j = 0; j + 1 < maxn; ++j) {
     for (int t = wid; t < cnt; t += HQ_WARPS) {
       const HMat& M = s_mat[t];
       const int k = s_col[t];
       if (k <= j || j + 1 >= M.n) continue;
-      apply_reflector(M, j, M.A + (size_t)k * M.m, lane);
-      if (k == j + 1) make_reflector(M, j + 1, lane);
+      if (k == j + 1) {
+        double nrm2;
+        double2 alpha;
+        apply_reflector<true>(M, j, M.A + (size_t)k * M.m, lane, &nrm2, &alpha);
+        finish_reflector(M, j + 1, nrm2, alpha, lane);
+      } else {
+        apply_reflector<false>(M, j, M.A + (size_t)k * M.m, lane);
+      }
     }
     if (!grid_barrier(gs, status)) return;
   }
@@ -218,7 +250,7 @@ __device__ __forceinline__ void hqr_body(const Get& get, int n_items, GridSync g
     __syncwarp();
     for (int r = lane; r < M.m; r += 32) __stcg(a + r, make_double2(r == k ? 1.0 : 0.0, 0.0));
     __syncwarp();
-    for (int j = min(k, M.n - 1); j >= 0; --j) apply_reflector(M, j, a, lane);
+    for (int j = min(k, M.n - 1); j >= 0; --j) apply_reflector<false>(M, j, a, lane);
   }
 }
 

@@ -135,10 +135,12 @@ constexpr int RSVD_OVERSAMPLE = 32;
 // power iterations: the subspace error at the cut chi falls like (s_{l+1} / s_chi)^(2q+1)
 constexpr int RSVD_POWER = 2;
 void launch_rsvd_omega(double2* Om, int rows, int cols, unsigned seed, cudaStream_t st);
-// the range finder up to the l x l factor in G64 (then: the Jacobi on it, launch_jacobi_grid with
-// on_b = 2; the truncation, k_truncate with rsvd = 1; the kept singular vectors into A and V)
-void launch_rsvd(const Tables& T, const BondWork* work, int n_work, const RsvdLists& L, int chi_max, int p,
-                 const double2* Om, int ld_om, int blocks, unsigned* sync3, cudaStream_t st);
+// the order of a layer: plan (item lists, l into info[9]); gy1 -> QR q1; RSVD_POWER times
+// (gz1 -> QR qz, gy2 -> QR q2); gz2; gres (D - Q Z^H); tail norm; QR qb (l x l factor into G64);
+// Jacobi on it (launch_jacobi_grid, on_b = 2); truncation (k_truncate, rsvd = 1); vectors
+void launch_rsvd_plan(const Tables& T, const BondWork* work, int n_work, const RsvdLists& L, int chi_max, int p,
+                      const double2* Om, int ld_om, cudaStream_t st);
+void launch_rsvd_tail_norm(const BondWork* work, int n_work, cudaStream_t st);
 void launch_rsvd_vectors(const Tables& T, const BondWork* work, int n_work, const RsvdLists& L, cudaStream_t st);
 
 // set the message returned by pt_tebd_last_error(NULL) (engine.cu)

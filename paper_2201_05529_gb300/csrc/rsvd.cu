@@ -157,23 +157,14 @@ void launch_rsvd_omega(double2* Om, int rows, int cols, unsigned seed, cudaStrea
   k_rsvd_omega<<<4 * 152, 256, 0, st>>>(Om, rows, cols, seed);
 }
 
-void launch_rsvd(const Tables& T, const BondWork* work, int n_work, const RsvdLists& L, int chi_max, int p,
-                 const double2* Om, int ld_om, int blocks, unsigned* sync3, cudaStream_t st) {
+void launch_rsvd_plan(const Tables& T, const BondWork* work, int n_work, const RsvdLists& L, int chi_max, int p,
+                      const double2* Om, int ld_om, cudaStream_t st) {
   k_rsvd_plan<<<(n_work + 127) / 128, 128, 0, st>>>(work, n_work, chi_max, p, Om, ld_om, L.gy1, L.gz1, L.gy2, L.gz2,
                                                      L.gres, L.q1, L.qz, L.q2, L.qb, T.status);
-  const int mc = L.m_cap, lc = L.l_cap;
-  launch_zgemm(L.gy1, n_work, L.tile_cap, mc, lc, T.status, st);      // Y = D Omega
-  launch_hqr_items(L.q1, n_work, blocks, sync3, T.status, st);
-  for (int it = 0; it < RSVD_POWER; ++it) {
-    launch_zgemm(L.gz1, n_work, L.tile_cap, mc, lc, T.status, st);    // Z = D^H Q
-    launch_hqr_items(L.qz, n_work, blocks, sync3, T.status, st);
-    launch_zgemm(L.gy2, n_work, L.tile_cap, mc, lc, T.status, st);    // Y = D Qz
-    launch_hqr_items(L.q2, n_work, blocks, sync3, T.status, st);
-  }
-  launch_zgemm(L.gz2, n_work, L.tile_cap, mc, lc, T.status, st);      // Z = D^H Q
-  launch_zgemm(L.gres, n_work, L.tile_cap, mc, mc, T.status, st);     // D - Q Z^H
+}
+
+void launch_rsvd_tail_norm(const BondWork* work, int n_work, cudaStream_t st) {
   k_rsvd_fro<<<n_work, 256, 0, st>>>(work, n_work);
-  launch_hqr_items(L.qb, n_work, blocks, sync3, T.status, st);            // Z = Qb Rb
 }
 
 void launch_rsvd_vectors(const Tables& T, const BondWork* work, int n_work, const RsvdLists& L, cudaStream_t st) {
