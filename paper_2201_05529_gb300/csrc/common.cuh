@@ -121,8 +121,9 @@ struct BondWork {
   double2* RH;             // [rs_mx * L_cap]  Householder vectors
   double2* RR;             // [L_cap * L_cap]  discarded triangular factors
   double* Rtau;            // [L_cap]
-  unsigned char* ZA;       // packed operands of the sliced tensor-core GEMMs
+  unsigned char* ZA;       // packed operands of the sliced tensor-core GEMMs (ZA: D or Q as A)
   unsigned char* ZB;
+  unsigned char* ZA2;      // D^H as the A operand, packed once per bond update
   int mL_cap, nL_cap, mR_cap, nR_cap, mD_cap, nD_cap, k_cap, pad2;
   int rs_mx, L_cap;        // max(mD_cap, nD_cap) and the range finder's capacity (0: no fast path)
 };

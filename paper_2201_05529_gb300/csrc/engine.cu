@@ -283,7 +283,10 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n, int layer) {
     ev_begin(h, 8, &e);
     ptk::launch_rsvd_plan(h->T, work, n, L, h->opt.chi_max, ptk::RSVD_OVERSAMPLE, h->d_omega, h->ld_omega, s);
     ev_end(h, e);
-    gemm(L.gy1, lc);                                    // Y = D Omega
+    gemm(L.gy1, lc);                                    // Y = D Omega (packs D)
+    ev_begin(h, 8, &e);
+    ptk::launch_zgemm_pack_a(L.gz1, n, mc, st, s);      // D^H, packed once for every D^H Q
+    ev_end(h, e);
     qr(L.q1);
     for (int it = 0; it < ptk::RSVD_POWER; ++it) {
       gemm(L.gz1, lc);                                  // Z = D^H Q
@@ -967,11 +970,12 @@ int build(pt_tebd* h) {
         W.RR = (double2*)h->dalloc(sizeof(double2) * L * L);
         W.Rtau = (double*)h->dalloc(sizeof(double) * L);
         W.ZA = (unsigned char*)h->dalloc(ptk::zgemm_pack_bytes(W.rs_mx, W.rs_mx, 0));
+        W.ZA2 = (unsigned char*)h->dalloc(ptk::zgemm_pack_bytes(W.rs_mx, W.rs_mx, 0));
         // B operands: up to L_cap columns with K up to rs_mx, or (the residual D - Q Z^H) up to
         // rs_mx columns with K up to L_cap
         W.ZB = (unsigned char*)h->dalloc(std::max(ptk::zgemm_pack_bytes(W.L_cap, W.rs_mx, 1),
                                                   ptk::zgemm_pack_bytes(W.rs_mx, W.L_cap, 1)));
-        if (!W.RY || !W.RZ || !W.RH || !W.RR || !W.Rtau || !W.ZA || !W.ZB)
+        if (!W.RY || !W.RZ || !W.RH || !W.RR || !W.Rtau || !W.ZA || !W.ZA2 || !W.ZB)
           return h->fail(PT_ERR_OOM, "fast-path SVD scratch");
       }
       {

@@ -26,6 +26,8 @@ constexpr int HQ_THREADS = 512;
 constexpr int HQ_WARPS = HQ_THREADS / 32;
 constexpr int HQ_MAX_PAIRS = 384;           // (block, column) pairs one CTA may own
 constexpr int HQ_MAX_ITEMS = 2048;          // blocks: two per bond
+constexpr int HQ_U = 8;                     // rows per lane per block: loads in flight per lane
+constexpr int HQ_ROWS = 32 * HQ_U;          // rows per block
 
 using HMat = QRItem;
 
@@ -55,7 +57,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // s_j = 1 / (alpha - beta) is kept in H[j, j] (the slot of the implicit unit entry); so forming a
 // reflector needs no pass of its own over the column.
 
-// y <- P_j y on rows j.. (one warp). Four rows per lane per iteration: four independent L2 loads
+// y <- P_j y on rows j.. (one warp). HQ_U rows per lane per block: that many independent L2 loads
 // in flight per lane (the loops are latency-bound, not bandwidth-bound). With NORM, also return
 // ||y_new[j+1..]||^2 and alpha = y_new[j+1], and copy y_new[j+2..] raw into H[:, j+1] (the next
 // reflector's column).
@@ -67,30 +69,29 @@ __device__ __forceinline__ void apply_reflector(const HMat& M, int j, double2* y
   const double2* x = M.H + (size_t)j * M.m;
   const double2 sj = __ldcg(x + j);
   double2* hn = M.H + (size_t)(j + 1) * M.m;
-  // rows j+1 .. m-1 in blocks of 128 (lane + 32 q, q < 4); the block count is the same for every
+  // rows j+1 .. m-1 in blocks of HQ_ROWS (lane + 32 q, q < HQ_U); the block count is the same for every
   // lane, the last block's rows are predicated: no lane-dependent loop bounds
   const int r0 = j + 1 + lane;
-  const int nblk = (M.m - (j + 1) + 127) >> 7;
+  const int nblk = (M.m - (j + 1) + HQ_ROWS - 1) / HQ_ROWS;
   // pass 1: conj(x) . y over rows > j
   double sr0 = 0.0, si0 = 0.0, sr1 = 0.0, si1 = 0.0;
   if (t != 0.0) {
     for (int i = 0; i < nblk; ++i) {
-      const int r = r0 + (i << 7);
-      double2 a[4], b[4];
+      const int r = r0 + i * HQ_ROWS;
+      double2 a[HQ_U], b[HQ_U];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < HQ_U; ++q) {
         const bool in = r + 32 * q < M.m;
         a[q] = in ? __ldcg(x + r + 32 * q) : make_double2(0.0, 0.0);
         b[q] = in ? __ldcg(y + r + 32 * q) : make_double2(0.0, 0.0);
       }
-      sr0 = fma(a[0].x, b[0].x, fma(a[0].y, b[0].y, sr0));
-      si0 = fma(a[0].x, b[0].y, fma(-a[0].y, b[0].x, si0));
-      sr1 = fma(a[1].x, b[1].x, fma(a[1].y, b[1].y, sr1));
-      si1 = fma(a[1].x, b[1].y, fma(-a[1].y, b[1].x, si1));
-      sr0 = fma(a[2].x, b[2].x, fma(a[2].y, b[2].y, sr0));
-      si0 = fma(a[2].x, b[2].y, fma(-a[2].y, b[2].x, si0));
-      sr1 = fma(a[3].x, b[3].x, fma(a[3].y, b[3].y, sr1));
-      si1 = fma(a[3].x, b[3].y, fma(-a[3].y, b[3].x, si1));
+#pragma unroll
+      for (int q = 0; q < HQ_U; q += 2) {
+        sr0 = fma(a[q].x, b[q].x, fma(a[q].y, b[q].y, sr0));
+        si0 = fma(a[q].x, b[q].y, fma(-a[q].y, b[q].x, si0));
+        sr1 = fma(a[q + 1].x, b[q + 1].x, fma(a[q + 1].y, b[q + 1].y, sr1));
+        si1 = fma(a[q + 1].x, b[q + 1].y, fma(-a[q + 1].y, b[q + 1].x, si1));
+      }
     }
   }
   const double dr = warp_sum(sr0 + sr1), di = warp_sum(si0 + si1);
@@ -104,16 +105,16 @@ __device__ __forceinline__ void apply_reflector(const HMat& M, int j, double2* y
   double n0 = 0.0, n1 = 0.0;
   double2 alpha = make_double2(0.0, 0.0);
   for (int i = 0; i < nblk; ++i) {
-    const int r = r0 + (i << 7);
-    double2 a[4], b[4];
+    const int r = r0 + i * HQ_ROWS;
+    double2 a[HQ_U], b[HQ_U];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < HQ_U; ++q) {
       const bool in = r + 32 * q < M.m;
       a[q] = in ? __ldcg(x + r + 32 * q) : make_double2(0.0, 0.0);
       b[q] = in ? __ldcg(y + r + 32 * q) : make_double2(0.0, 0.0);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < HQ_U; ++q) {
       const int rr = r + 32 * q;
       if (rr >= M.m) continue;
       if (t != 0.0) {

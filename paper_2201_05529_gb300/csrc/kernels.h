@@ -115,8 +115,11 @@ struct ZGemmItem {
   int cap_m, cap_n, cap_k;
   int* flag;               // set to 1 when a product entry is not finite (NULL: not reported)
   int acc;                 // 0: C = opA(A) opB(B); -1: C = C - opA(A) opB(B)
+  int skip_a;              // 1: A's slice planes and row exponents are already in TA (packed earlier)
 };
 size_t zgemm_pack_bytes(int rows_cap, int k_cap, int which);
+// the A operands' slice planes and row exponents alone (for items whose later products skip them)
+void launch_zgemm_pack_a(const ZGemmItem* items, int n_items, int m_cap_max, int* status, cudaStream_t st);
 int zgemm_tile_cap(int m_cap, int n_cap);
 // tile_cap: total output tiles of the item list at capacity (the persistent grid's upper bound);
 // m_cap_max / n_cap_max: the largest M and N capacities (pack grid sizes)

@@ -91,6 +91,11 @@ __global__ void k_rsvd_plan(const BondWork* work, int n_work, int chi_max, int p
   gy1[w] = zitem(W, W.A, Ma, ZOP_N, Om, ld_om, ZOP_N, W.RY, max(Ma, 1), Ma, l, Na, nullptr);
   gz1[w] = zitem(W, W.A, Ma, ZOP_C, W.RY, max(Ma, 1), ZOP_N, W.RZ, max(Na, 1), Na, l, Ma, nullptr);
   gy2[w] = zitem(W, W.A, Ma, ZOP_N, W.RZ, max(Na, 1), ZOP_N, W.RY, max(Ma, 1), Ma, l, Na, nullptr);
+  // D is packed once into ZA (by the first product, Y = D Omega) and D^H once into ZA2 (a pack-only
+  // launch before the power iterations): the later products with D skip their A packing
+  gy2[w].skip_a = 1;
+  gz1[w].TA = W.ZA2;
+  gz1[w].skip_a = 1;
   gz2[w] = gz1[w];
   // D <- D - Q Z^H (Z = D^H Q): what lies outside span(Q), whose norm is the lumped tail
   ZGemmItem r = zitem(W, W.RY, max(Ma, 1), ZOP_N, W.RZ, max(Na, 1), ZOP_C, W.A, max(Ma, 1), Ma, Na, l, nullptr);

@@ -80,11 +80,14 @@ __device__ __forceinline__ double2 op_elem(const ZGemmItem& it, int which, int r
 
 // Pass 1: e with max |entry| < 2^e for every row of opA(A) (which = 0) or column of opB(B) (1).
 // grid: (x: rows, y: items)
+// which = -1: operand A even where the item marks it as already packed (a pack-only launch)
 __global__ void k_zg_rowexp(const ZGemmItem* items, int n_items, int which) {
   const int i = blockIdx.y;
   if (i >= n_items) return;
   const ZGemmItem it = items[i];
-  if (!item_live(it) || !item_fits(it)) return;
+  const bool force = which < 0;
+  if (force) which = 0;
+  if (!item_live(it) || !item_fits(it) || (which == 0 && it.skip_a > 0 && !force)) return;
   const int rows = which == 0 ? it.M : it.N, tr = which == 0 ? TMA : TNB;
   const PackCap cp = zcap(it, which);
   int* ex = (int*)((which == 0 ? it.TA : it.TB) + cp.exp_off);
@@ -107,7 +110,9 @@ __global__ void k_zg_pack(const ZGemmItem* items, int n_items, int which, int* s
   const int i = blockIdx.y;
   if (i >= n_items) return;
   const ZGemmItem it = items[i];
-  if (!item_live(it)) return;
+  const bool force = which < 0;
+  if (force) which = 0;
+  if (!item_live(it) || (which == 0 && it.skip_a > 0 && !force)) return;
   if (!item_fits(it)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_CAPACITY);
     return;
@@ -358,6 +363,13 @@ namespace {
 constexpr int ZMAX_DEV = 64;
 bool g_zattr_done[ZMAX_DEV] = {};
 }  // namespace
+
+void launch_zgemm_pack_a(const ZGemmItem* items, int n_items, int m_cap_max, int* status, cudaStream_t st) {
+  if (n_items <= 0) return;
+  const int bx_a = std::min(64, cdiv(std::max(1, m_cap_max), 128));
+  k_zg_rowexp<<<dim3(bx_a, n_items), 128, 0, st>>>(items, n_items, -1);
+  k_zg_pack<<<dim3(128, n_items), 256, 0, st>>>(items, n_items, -1, status);
+}
 
 void launch_zgemm(const ZGemmItem* items, int n_items, int tile_cap, int m_cap_max, int n_cap_max, int* status,
                   cudaStream_t st) {
