@@ -457,26 +457,44 @@ def run_ours(args, rank, world, local):
     if fp64_svd is not None:
         roofline["fp64_path_svd"] = fp64_svd
 
-    # --- end to end through the C ABI: host inputs -> init (H2D) -> W + K steps -> history (D2H);
-    # the work counted is the K-step window's only, while the timed region also holds the init and
-    # the W warm-up steps: a lower bound on the window's end-to-end rate
+    # --- end to end through the C ABI on the same steps W..W+K. The state after the W warm-up steps
+    # is read to the host once (a checkpoint, untimed). The timed region then initialises a handle
+    # from host buffers only (the augmented MPS at step W, the gates, the PT-MPOs cut at step W: every
+    # input of the window goes host -> device), runs the K steps and reads their observables and
+    # traces back to the host. One untimed handle of the same shapes is built and destroyed first,
+    # so the tuner's cache and the loaded modules are warm, as for a user's repeated job.
+    ck_eng = make(args.precision)
+    ck_eng.step(W)
+    ckpt = ck_eng.checkpoint()
+    ck_eng.destroy()
+    rchains, rmpos = capi.resume_problem(chains, mpos, ckpt)
+
+    def make_resumed():
+        e = capi.Engine(rchains, rmpos, chi_max=w.chi_max, eps=w.eps, precision=args.precision,
+                        multiplet_tol=w.multiplet_tol, max_steps=K, use_graph=True)
+        e.set_observables([Z])
+        return e
+
+    make_resumed().destroy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2 = make(args.precision)
-    e2.step(W + K)
-    hist, tr = e2.read_history(0, W + K + 1)
+    e2 = make_resumed()
+    e2.step(K)
+    hist, tr = e2.read_history(0, K + 1)
     t1 = time.perf_counter()
     e2.destroy()
     h2d = 0
-    for c in chains:
-        h2d += c["rho0"].nbytes if c.get("rho0") is not None else 0
+    for c in rchains:
+        h2d += sum(g.nbytes for g in c["gamma0"]) + sum(l.nbytes for l in c["lambda0"])
         h2d += (c["gates_q"].nbytes + c["gates_h"].nbytes) if c["N"] > 1 else 0
-    h2d += sum(P.nbytes for Ps in mpos for P in Ps)
+    h2d += sum(P.nbytes for Ps in rmpos for P in Ps)
     d2h = hist.nbytes + tr.nbytes
     e2e = {"value": site_steps_per_step * K / (t1 - t0), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d / K), "d2h_bytes_per_step": int(d2h / K),
-           "window": f"steps {W}..{W + K} counted; timed: init (all host inputs to the device) + steps "
-                     f"0..{W + K} + the history read"}
+           "window": f"steps {W}..{W + K}, the same steps as value; timed: init from host buffers (the "
+                     f"checkpointed state at step {W}, gates, PT-MPOs from step {W + 1}) + {K} steps + the "
+                     f"history read",
+           "max_sz_diff_vs_timed_run": float(np.max(np.abs(hist - hist_fast)))}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",

@@ -60,7 +60,7 @@ typedef enum {
                        7-bit slices; the leading slice products sum exactly in FP32 accumulators over
                        K chunks of 512, Ozaki's error-free splitting; ~1e-12 of the operands' scale).
                        theta + gate is one such GEMM; the bond SVD is a randomized truncated SVD
-                       (range finder of width l = min(n, chi_max + 32) with one power iteration, its
+                       (range finder of width l = min(n, chi_max + 32) with two power iterations, its
                        products on the tensor cores, FP64 Householder QR and an FP64 Jacobi SVD of
                        the l x l factor; the part of D outside the range counts as one discarded
                        singular value). Its singular values are accurate to ~1e-11 of sigma_max, so
@@ -163,6 +163,16 @@ int pt_tune_cache_store(const char* path, const char* key, int qr, int k2);
 int pt_tebd_get_dims(pt_tebd_t h, int chain, int* chi, int* kappa);
 int pt_tebd_get_lambda(pt_tebd_t h, int chain, int bond, double* out, int cap);
 int pt_tebd_get_lognorm(pt_tebd_t h, int chain, double* out);
+
+/* Checkpoint read of one site tensor (App. B.2 continues a propagation from the full augmented MPS):
+ * copies Gamma_n of `site` (0-based) of `chain` into out as complex [chi_{n-1}][4][kappa_n][chi_n]
+ * (interleaved re, im; the live dims of pt_tebd_get_dims), the layout pt_chain_desc.gamma0 takes.
+ * cap is out's size in complex elements; out may be NULL to ask for the size. Synchronous; returns
+ * the element count, PT_ERR_ARG when cap is too small. Together with pt_tebd_get_lambda and
+ * pt_tebd_get_lognorm it gives a resumable state: a new handle initialised with these tensors as
+ * gamma0 / lambda0, the log-norm folded into one Gamma, and every PT-MPO cut at the current step
+ * (its tensors from P^(k+1) on, kappa[0] = the site's current kappa) continues the same run. */
+int pt_tebd_get_gamma(pt_tebd_t h, int chain, int site, double* out, size_t cap);
 
 /* Jacobi sweeps of the most recent update of every bond (odd-layer bonds first, then even):
  * out[2i] = FP64 sweeps (negative: the bond hit max_sweeps), out[2i+1] = the update's fault flags

@@ -24,7 +24,7 @@ ERRORS = {-1: "PT_ERR_ARG", -2: "PT_ERR_OOM", -3: "PT_ERR_CAPACITY", -4: "PT_ERR
 EXPORTS = [
     "pt_tebd_set_allocator", "pt_tebd_init", "pt_tebd_set_observables", "pt_tebd_step",
     "pt_tebd_observe", "pt_tebd_read_history", "pt_tebd_apply_local", "pt_tebd_steps_done",
-    "pt_tebd_get_dims", "pt_tebd_get_lambda", "pt_tebd_get_lognorm", "pt_tebd_get_svd_sweeps",
+    "pt_tebd_get_dims", "pt_tebd_get_lambda", "pt_tebd_get_lognorm", "pt_tebd_get_gamma", "pt_tebd_get_svd_sweeps",
     "pt_tebd_clone", "pt_tebd_read_bond_log", "pt_tebd_step_kernels", "pt_tebd_get_routes",
     "pt_tune_cache_lookup", "pt_tune_cache_store",
     "pt_tebd_sync", "pt_tebd_destroy", "pt_tebd_last_error", "pt_tebd_set_timing",
@@ -95,6 +95,7 @@ lib.pt_tune_cache_store.argtypes = [C.c_char_p, C.c_char_p, C.c_int, C.c_int]
 lib.pt_tebd_get_dims.argtypes = [C.c_void_p, C.c_int, c_int_p, c_int_p]
 lib.pt_tebd_get_lambda.argtypes = [C.c_void_p, C.c_int, C.c_int, c_double_p, C.c_int]
 lib.pt_tebd_get_lognorm.argtypes = [C.c_void_p, C.c_int, c_double_p]
+lib.pt_tebd_get_gamma.argtypes = [C.c_void_p, C.c_int, C.c_int, c_double_p, C.c_size_t]
 lib.pt_tebd_get_svd_sweeps.argtypes = [C.c_void_p, c_int_p, C.c_int]
 lib.pt_tebd_clone.argtypes = [C.c_void_p, C.POINTER(C.c_void_p)]
 lib.pt_tebd_read_bond_log.argtypes = [C.c_void_p, C.c_int, C.c_int, c_int_p, C.c_size_t]
@@ -312,6 +313,28 @@ class Engine:
         _check(lib.pt_tebd_get_lognorm(self.h, int(chain), C.byref(v)), self.h)
         return v.value
 
+    def get_gamma(self, chain, site):
+        """pt_tebd_get_gamma: Gamma_n of one site, complex [chi_{n-1}][4][kappa_n][chi_n]."""
+        chi, kap = self.get_dims(chain)
+        shape = (int(chi[site]), 4, int(kap[site]), int(chi[site + 1]))
+        out = np.zeros(shape, dtype=np.complex128)
+        n = _check(lib.pt_tebd_get_gamma(self.h, int(chain), int(site), _dptr(out), out.size), self.h)
+        assert n == out.size
+        return out
+
+    def checkpoint(self):
+        """The full augmented MPS of every chain at the current step (App. B.2), on the host:
+        [{'step', 'chi', 'kappa', 'gamma': [N], 'lambda': [N + 1], 'lognorm'}]."""
+        step = self.steps_done()
+        out = []
+        for c in range(self.n_chains):
+            chi, kap = self.get_dims(c)
+            out.append({"step": step, "chi": chi.copy(), "kappa": kap.copy(),
+                        "gamma": [self.get_gamma(c, n) for n in range(self.N[c])],
+                        "lambda": [self.get_lambda(c, b)[:int(chi[b])].copy() for b in range(self.N[c] + 1)],
+                        "lognorm": self.get_lognorm(c)})
+        return out
+
     def get_svd_sweeps(self, cap=4096):
         """[(Jacobi sweeps, fault flags)] of the latest update of every bond (odd layer first)."""
         out = np.zeros(2 * cap, dtype=np.int32)
@@ -356,6 +379,28 @@ class Engine:
             self.destroy()
         except Exception:
             pass
+
+
+def resume_problem(chains, pt_mpos, ckpt):
+    """Inputs of pt_tebd_init that continue a run from a checkpoint (Engine.checkpoint) taken after
+    step s: every chain starts from its augmented MPS at step s, its log-norm folded into the first
+    site tensor (exp(lognorm) Gamma_1: the state, and so every raw Tr(O rho), is unchanged), and every
+    PT-MPO is cut to its tensors P^(s+1), ... (its bond kappa[s] becomes the first). History index 0
+    of the new handle is step s of the original run."""
+    steps = {int(ck["step"]) for ck in ckpt}
+    if len(steps) != 1:
+        raise ValueError("checkpoint chains are at different steps")
+    s = steps.pop()
+    out = []
+    for ch, ck in zip(chains, ckpt):
+        d = dict(ch)
+        gam = [np.array(g, dtype=np.complex128) for g in ck["gamma"]]
+        gam[0] = gam[0] * np.exp(ck["lognorm"])
+        d.update(rho0=None, chi0=np.asarray(ck["chi"], dtype=np.int32),
+                 kappa0=np.asarray(ck["kappa"], dtype=np.int32), gamma0=gam,
+                 lambda0=[np.asarray(l, dtype=np.float64) for l in ck["lambda"]])
+        out.append(d)
+    return out, [list(Ps[s:]) for Ps in pt_mpos]
 
 
 def svd_scratch_bytes(m, n, batch):

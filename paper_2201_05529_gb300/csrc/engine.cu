@@ -1427,6 +1427,26 @@ int pt_tebd_get_lognorm(pt_tebd_t h, int chain, double* out) {
   return rc;
 }
 
+int pt_tebd_get_gamma(pt_tebd_t h, int chain, int site, double* out, size_t cap) {
+  if (!h || chain < 0 || chain >= h->n_chains || site < 0 || site >= h->chains[chain].N) return PT_ERR_ARG;
+  const int s = h->site0[chain] + site, B = h->lam0[chain] + site;
+  int chi[2] = {0, 0}, kap = 0;
+  double2* cur = nullptr;
+  cudaMemcpyAsync(chi, h->T.lam_chi + B, sizeof(int) * 2, cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(&kap, h->T.site_kappa + s, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(&cur, h->T.site_gam + s, sizeof(double2*), cudaMemcpyDeviceToHost, h->stream);
+  int rc = read_status(h);
+  if (rc != PT_OK) return rc;
+  const size_t n = (size_t)chi[0] * 4 * kap * chi[1];
+  if (out) {
+    if (cap < n) return h->fail(PT_ERR_ARG, "get_gamma: output holds fewer than chi_l * 4 * kappa * chi_r elements");
+    cudaMemcpyAsync(out, cur, sizeof(double2) * n, cudaMemcpyDeviceToHost, h->stream);
+    rc = read_status(h);
+    if (rc != PT_OK) return rc;
+  }
+  return (int)n;
+}
+
 int pt_tebd_clone(pt_tebd_t h, pt_tebd_t* out) {
   if (!h || !out) return PT_ERR_ARG;
   *out = nullptr;

@@ -47,3 +47,25 @@ def test_init_rejects_bad_arguments_without_a_gpu(capi):
 def test_svd_scratch_size_is_positive(capi):
     assert capi.svd_scratch_bytes(256, 256, 4) >= 256 * 256 * 16 * 4
     assert capi.svd_scratch_bytes(0, 4, 1) == 0
+
+
+def test_resume_problem_cuts_the_pt_mpos_and_folds_the_log_norm(capi):
+    import numpy as np
+    rng = np.random.default_rng(3)
+    chis, kaps = [1, 2, 3, 1], [2, 1, 3]
+    gam = [rng.normal(size=(chis[n], 4, kaps[n], chis[n + 1])) + 0j for n in range(3)]
+    lam = [np.ones(c) for c in chis]
+    P = [rng.normal(size=(1 if k == 0 else 2, 4, 4, 2)) + 0j for k in range(6)]
+    Q = [rng.normal(size=(1 if k == 0 else 3, 4, 4, 3)) + 0j for k in range(6)]
+    chains = [dict(N=3, rho0=np.zeros((3, 4)), gates_q=np.zeros((2, 16, 16)), gates_h=np.zeros((2, 16, 16)),
+                   ptmpo_id=[0, -1, 1])]
+    ck = [{"step": 4, "chi": np.array(chis), "kappa": np.array(kaps), "gamma": gam, "lambda": lam, "lognorm": -0.75}]
+    rc, rm = capi.resume_problem(chains, [P, Q], ck)
+    assert [len(x) for x in rm] == [2, 2] and rm[0][0] is P[4] and rm[1][1] is Q[5]
+    d = rc[0]
+    assert d["rho0"] is None and list(d["chi0"]) == chis and list(d["kappa0"]) == kaps
+    assert np.allclose(d["gamma0"][0], gam[0] * np.exp(-0.75)) and d["gamma0"][1] is not gam[1]
+    assert np.array_equal(d["gamma0"][2], gam[2]) and d["ptmpo_id"] == [0, -1, 1]
+    assert chains[0]["rho0"] is not None                   # the caller's dicts are not modified
+    with pytest.raises(ValueError):
+        capi.resume_problem(chains + chains, [P, Q], ck + [dict(ck[0], step=5)])

@@ -90,6 +90,42 @@ def test_ensemble_of_four_chains_twenty_steps():
     eng.destroy()
 
 
+def test_full_ensemble_of_64_chains_in_one_engine():
+    # all 64 chains (N = 4..16, two end baths each, 128 PT-MPOs) in one handle: every layer is one
+    # grouped launch over the bonds of every chain. Eight chains spread over the batch (short and
+    # long ones) against the oracle element by element (FP64 path, 1e-9, bond dimensions exact);
+    # the fast path on the same batch against the FP64 path (1e-5) and the trace of every chain.
+    import paper_2201_05529_gb300._capi as capi
+    from tests.gpu_helpers import engine_args_from_oracle
+    K = 10
+    w = workload("xyz_ensemble64", K=K)
+    cis = oprob.build_inputs(w)
+    assert len(cis) == 64
+    chains, mpos = engine_args_from_oracle(cis)
+    out = {}
+    for prec in ("fp64", "bf16_ozaki"):
+        eng = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, precision=prec,
+                          multiplet_tol=w.multiplet_tol, max_steps=K)
+        eng.set_observables(OPS)
+        eng.step(K)
+        obs, tr = eng.read_history(0, K + 1)
+        dims = [eng.get_dims(c) for c in range(64)]
+        eng.destroy()
+        out[prec] = (obs, tr, dims)
+    obs, tr, dims = out["fp64"]
+    sel = [0, 9, 18, 27, 36, 45, 54, 63]
+    refs = run_oracle(w, [cis[c] for c in sel], OPS, K=K)
+    for c, r in zip(sel, refs):
+        N = cis[c].N
+        err = float(np.max(np.abs(obs[:, c, :N, :] - r.obs)))
+        assert err < TOL, f"chain {c} (N = {N}): max |obs - oracle| = {err:.3e}"
+        assert list(dims[c][0]) == list(r.chis[-1]), f"chain {c}: bond dimensions"
+        assert np.max(np.abs(tr[:, c] - r.trace)) < TOL
+    assert np.max(np.abs(tr - 1.0)) < 1e-3                       # PT-MPO compression only
+    fobs, ftr, _ = out["bf16_ozaki"]
+    assert np.max(np.abs(fobs - obs)) < 1e-5 and np.max(np.abs(ftr - tr)) < 1e-5
+
+
 def test_random_stress_state_singular_values():
     # the stress workload's structure (Gaussian augmented MPS, Gaussian PT tensors, Haar gates) at
     # N=8, chi=32, kappa=8 for 2 steps: bond dims and singular values against the oracle
