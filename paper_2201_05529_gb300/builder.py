@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpttebd.so")
-SOURCES = ["kernels_f64.cu", "jacobi_cluster.cu", "jacobi_grid.cu", "tc_theta.cu", "svd_gemm.cu", "qrcp.cu", "engine.cu", "selftest.cu", "svd_noalloc.cu", "hqr_grid.cu", "tc_zgemm.cu", "rsvd.cu"]
+SOURCES = ["kernels_f64.cu", "jacobi_cluster.cu", "jacobi_grid.cu", "tc_theta.cu", "svd_gemm.cu", "qrcp.cu", "engine.cu", "selftest.cu", "svd_noalloc.cu", "hqr_grid.cu", "tc_zgemm.cu", "rsvd.cu", "tc_contract.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -108,6 +108,15 @@ struct pt_tebd {
   SiteWork* d_sites = nullptr;
   int n_site_work = 0;
   int gx_site = 1;
+  // fast path: the site layer as one sliced tensor-core GEMM, one item per site (tc_contract.cu)
+  ptk::ZGemmItem* d_site_items = nullptr;
+  int site_tile_cap = 0, site_mcap = 1, site_ncap = 1;
+  // fast path: the Gamma recovery as sliced tensor-core GEMMs, two items per bond (tc_contract.cu)
+  struct RecList {
+    ptk::ZGemmItem* items = nullptr;
+    int** bcols = nullptr;
+    int tile_cap = 0, mcap = 1, ncap = 1;
+  } rec_odd, rec_even;
 
   // observables
   double2* d_ops = nullptr;
@@ -349,7 +358,11 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n, int layer) {
     ev_end(h, e);
   }
   ev_begin(h, 5, &e);
-  ptk::k_recover<<<dim3(h->gx_bond, n), 256, 0, s>>>(h->T, work, n);
+  const pt_tebd::RecList& RL = work == h->d_odd ? h->rec_odd : h->rec_even;
+  if (RL.items)
+    ptk::launch_recover_tc(h->T, work, n, RL.items, RL.bcols, h->gx_bond, RL.tile_cap, RL.mcap, RL.ncap, s);
+  else
+    ptk::k_recover<<<dim3(h->gx_bond, n), 256, 0, s>>>(h->T, work, n);
   ev_end(h, e);
   ptk::k_bond_log<<<(n + 127) / 128, 128, 0, s>>>(h->T, work, n, layer, h->d_blog, h->hist_cap, h->blog_nb);
 }
@@ -377,8 +390,12 @@ void enqueue_step(pt_tebd* h) {
   if (h->n_site_work > 0) {
     cudaEvent_t e = nullptr;
     ev_begin(h, 0, &e);
-    ptk::k_site_contract<<<dim3(h->gx_site, h->n_site_work), 256, 0, h->stream>>>(h->T, h->d_sites,
-                                                                                 h->n_site_work);
+    if (h->d_site_items)
+      ptk::launch_site_tc(h->T, h->d_sites, h->n_site_work, h->d_site_items, h->gx_site, h->site_tile_cap,
+                          h->site_mcap, h->site_ncap, h->stream);
+    else
+      ptk::k_site_contract<<<dim3(h->gx_site, h->n_site_work), 256, 0, h->stream>>>(h->T, h->d_sites,
+                                                                                   h->n_site_work);
     ptk::k_site_swap<<<(h->n_site_work + 127) / 128, 128, 0, h->stream>>>(h->T, h->d_sites,
                                                                           h->n_site_work);
     ev_end(h, e);
@@ -1103,6 +1120,47 @@ int build(pt_tebd* h) {
   h->d_even = even.empty() ? nullptr : upload(h, even);
   h->gx_bond = (int)std::min<size_t>(256, (max_bond_elems + 255) / 256);
 
+  if (h->use_rsvd) {
+    // the fast path's Gamma recovery on the tensor cores: per bond a left item (Q_L times U, C in HH)
+    // and a right item (Q_R^H times V, C in HH + mL_cap nL_cap), packed planes at capacity
+    auto rec_list = [&](const std::vector<BondWork>& v, pt_tebd::RecList& R) -> int {
+      if (v.empty() || 2 * (int)v.size() > ptk::zgemm_max_items()) return PT_OK;
+      std::vector<ptk::ZGemmItem> items(2 * v.size());
+      std::vector<int*> bc(v.size());
+      long long tiles = 0;
+      for (size_t w = 0; w < v.size(); ++w) {
+        const BondWork& W = v[w];
+        bc[w] = (int*)h->dalloc(sizeof(int) * (size_t)(W.nL_cap + W.mR_cap));
+        if (!bc[w]) return h->fail(PT_ERR_OOM, "tensor-core recovery column maps");
+        for (int side = 0; side < 2; ++side) {
+          ptk::ZGemmItem& it = items[2 * w + side];
+          it = ptk::ZGemmItem{};
+          it.cap_m = side == 0 ? W.mL_cap : W.nR_cap;
+          it.cap_k = side == 0 ? std::min(W.mL_cap, W.nL_cap) : std::min(W.nR_cap, W.mR_cap);
+          it.cap_n = side == 0 ? W.nL_cap : W.mR_cap;
+          it.opA = ptk::ZOP_N;
+          it.opB = side == 0 ? ptk::ZOP_T : ptk::ZOP_N;
+          it.bcol = side == 0 ? bc[w] : bc[w] + W.nL_cap;
+          it.C = side == 0 ? W.HH : W.HH + (size_t)W.mL_cap * W.nL_cap;
+          it.TA = (unsigned char*)h->dalloc(ptk::zgemm_pack_bytes(it.cap_m, it.cap_k, 0));
+          it.TB = (unsigned char*)h->dalloc(ptk::zgemm_pack_bytes(it.cap_n, it.cap_k, 1));
+          if (!it.TA || !it.TB) return h->fail(PT_ERR_OOM, "tensor-core recovery scratch");
+          tiles += ptk::zgemm_tile_cap(it.cap_m, it.cap_n);
+          R.mcap = std::max(R.mcap, it.cap_m);
+          R.ncap = std::max(R.ncap, it.cap_n);
+        }
+      }
+      R.tile_cap = (int)std::min<long long>(tiles, 1 << 30);
+      R.items = upload(h, items);
+      R.bcols = upload(h, bc);
+      if (!R.items || !R.bcols) return h->fail(PT_ERR_OOM, "tensor-core recovery items");
+      return PT_OK;
+    };
+    int rc = rec_list(odd, h->rec_odd);
+    if (rc == PT_OK) rc = rec_list(even, h->rec_even);
+    if (rc != PT_OK) return rc;
+  }
+
   // site work list
   std::vector<SiteWork> sw;
   size_t max_site = 1;
@@ -1116,6 +1174,31 @@ int build(pt_tebd* h) {
   h->n_site_work = (int)sw.size();
   h->d_sites = sw.empty() ? nullptr : upload(h, sw);
   h->gx_site = (int)std::min<size_t>(256, (max_site + 255) / 256);
+  if (h->opt.precision == PT_BF16_OZAKI && h->use_rsvd && !sw.empty() && h->n_site_work <= ptk::zgemm_max_items()) {
+    // the fast path's site layer on the tensor cores: per site the GEMM's output scratch and the
+    // packed slice planes of both operands at capacity; live fields are written by the plan kernel
+    std::vector<ptk::ZGemmItem> items(sw.size());
+    long long tiles = 0;
+    for (size_t w = 0; w < sw.size(); ++w) {
+      const int s = sw[w].site, B = sw[w].lam;
+      ptk::ZGemmItem& it = items[w];
+      it = ptk::ZGemmItem{};
+      it.cap_m = h->lam_cap_h[B] * h->lam_cap_h[B + 1];
+      it.cap_k = it.cap_n = 4 * h->kcap_h[s];
+      it.opA = ptk::ZOP_N;
+      it.opB = ptk::ZOP_T;
+      it.C = (double2*)h->dalloc(sizeof(double2) * std::max(h->site_cap_h[s], (size_t)it.cap_m * it.cap_n));
+      it.TA = (unsigned char*)h->dalloc(ptk::zgemm_pack_bytes(it.cap_m, it.cap_k, 0));
+      it.TB = (unsigned char*)h->dalloc(ptk::zgemm_pack_bytes(it.cap_n, it.cap_k, 1));
+      if (!it.C || !it.TA || !it.TB) return h->fail(PT_ERR_OOM, "tensor-core site contraction scratch");
+      tiles += ptk::zgemm_tile_cap(it.cap_m, it.cap_n);
+      h->site_mcap = std::max(h->site_mcap, it.cap_m);
+      h->site_ncap = std::max(h->site_ncap, it.cap_n);
+    }
+    h->site_tile_cap = (int)std::min<long long>(tiles, 1 << 30);
+    h->d_site_items = upload(h, items);
+    if (!h->d_site_items) return h->fail(PT_ERR_OOM, "tensor-core site contraction items");
+  }
 
   // readout buffers
   h->ld = maxchi;

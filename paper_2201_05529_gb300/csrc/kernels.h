@@ -125,6 +125,20 @@ int zgemm_tile_cap(int m_cap, int n_cap);
 // m_cap_max / n_cap_max: the largest M and N capacities (pack grid sizes)
 void launch_zgemm(const ZGemmItem* items, int n_items, int tile_cap, int m_cap_max, int n_cap_max, int* status,
                   cudaStream_t st);
+// the most items one launch_zgemm takes
+int zgemm_max_items();
+
+// the fast path's PT site contraction on the tensor cores (tc_contract.cu): items[w] is site w's GEMM
+// (output scratch C, packed planes TA / TB and their capacities set at init; a plan kernel writes the
+// operands and live dims every step, so the launch sequence is graph-safe); writes Gamma' into the
+// sites' second buffers, to be swapped in by k_site_swap
+void launch_site_tc(const Tables& T, const SiteWork* work, int n_work, ZGemmItem* items, int gx, int tile_cap,
+                    int m_cap_max, int n_cap_max, cudaStream_t st);
+// the fast path's Gamma recovery on the tensor cores (tc_contract.cu): items[2w], items[2w + 1] are
+// bond w's left and right products (C in the bond's Householder scratch HH and HH + mL_cap nL_cap,
+// packed planes and caps set at init), bcols[w] its column maps (nL_cap + mR_cap ints)
+void launch_recover_tc(const Tables& T, const BondWork* work, int n_work, ZGemmItem* items, int* const* bcols,
+                       int gx, int tile_cap, int m_cap_max, int n_cap_max, cudaStream_t st);
 
 // the fast path's randomized truncated SVD of every bond of a layer (rsvd.cu): device item lists
 // (one entry per bond each) and their launch capacities

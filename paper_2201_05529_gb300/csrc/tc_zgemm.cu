@@ -357,6 +357,8 @@ size_t zgemm_pack_bytes(int rows_cap, int k_cap, int which) {
   return pack_cap(std::max(1, rows_cap), std::max(1, k_cap), which == 0 ? TMA : TNB, ZG::KSTEP, ZNS).total;
 }
 
+int zgemm_max_items() { return MAX_ITEMS; }
+
 int zgemm_tile_cap(int m_cap, int n_cap) { return cdiv(std::max(1, m_cap), TMA) * cdiv(std::max(1, n_cap), TNB); }
 
 namespace {
