@@ -55,6 +55,8 @@ def parse():
     # a smaller case of the same kernels (lower bond cap, smaller capacity buffers), for profiling
     ap.add_argument("--chi-max", type=int, default=0)
     ap.add_argument("--no-fp64-path", action="store_true")
+    # profiling aid: write the timed handle's bond log of steps 0..W+K ([step][layer][bond][field], .npy)
+    ap.add_argument("--bond-log", default="")
     return ap.parse_args()
 
 
@@ -178,6 +180,18 @@ def rsvd_flops(rec):
     return qr, gemm
 
 
+def sketch_elements(rec):
+    """Sketch elements m l the range finder's QRs factor over the window: (1 + q) m x l sketches Y and
+    (q + 1) n x l sketches Z per bond update (bond log [K, 6, nb, >=3])."""
+    tot = 0.0
+    q = RSVD_POWER
+    for r in rec.reshape(-1, rec.shape[-1]):
+        mD, nD, l = int(r[0]), int(r[1]), int(r[2])
+        if mD > 0 and nD > 0 and l > 0:
+            tot += ((1 + q) * max(mD, nD) + (q + 1) * min(mD, nD)) * l
+    return tot
+
+
 def bond_sizes(chis, kaps, N):
     """(m_L, n_L, m_R, n_R, r_L, r_R, chi) of every bond for the given dims (App. A.2)."""
     out = []
@@ -227,9 +241,11 @@ def aggregate(total_ms, site_steps_local, dist=None, device="cpu"):
     return work / (total_ms / 1e3), total_ms
 
 
-def traffic_record(kernel_src):
+def traffic_record(kernel_src, elements_per_launch=None):
     """DRAM bytes per launch of the dominant stage from a committed ncu capture, or None once the
-    kernel source has changed since that capture (the record carries the source's SHA-256)."""
+    kernel source has changed since that capture (the record carries the source's SHA-256). A record
+    taken on a smaller case gives bytes per sketch element; it is scaled by this run's elements per
+    launch (elements_per_launch)."""
     if not os.path.exists(TRAFFIC_FILE):
         return None, "no ncu capture recorded"
     try:
@@ -240,8 +256,10 @@ def traffic_record(kernel_src):
     for f in rec.get("sources", []):
         p = os.path.join(ROOT, "paper_2201_05529_gb300", "csrc", f)
         sha[f] = hashlib.sha256(open(p, "rb").read()).hexdigest()[:16] if os.path.exists(p) else None
-    if any(sha[f] != rec.get("sha", {}).get(f) for f in sha) or not sha:
-        return None, "kernel changed since the ncu capture"
+    if any(sha[f] != rec.get("sha", {}).get(f) for f in sha) or not sha or sorted(sha) != sorted(kernel_src):
+        return None, "no ncu capture of this kernel's current source"
+    if "dram_bytes_per_sketch_element" in rec and elements_per_launch:
+        return rec["dram_bytes_per_sketch_element"] * elements_per_launch, rec.get("how", "")
     return rec.get("dram_bytes_per_launch"), rec.get("how", "")
 
 
@@ -326,8 +344,11 @@ def run_ours(args, rank, world, local):
                                 dist if world > 1 else None, device="cuda")
     eng.sync()
     launches_per_step = eng.step_kernels()
+    routes = eng.routes()
     hist_fast, _ = eng.read_history(W, K + 1)
     blog, disc = eng.read_bond_log(W, K)
+    if args.bond_log:
+        np.save(args.bond_log, eng.read_bond_log(0, W + K)[0])
     dims = [eng.get_dims(c) for c in range(n_chains)]
     eng.destroy()
     fl_rest = fl_theta = 0.0
@@ -405,7 +426,7 @@ def run_ours(args, rank, world, local):
         n_qr = (1 + RSVD_POWER) + (RSVD_POWER + 1)          # QR launches per layer
         qr_ms = stage[7] / K / n_layers / n_qr              # per launch
         achieved = (fl_qr / (K * n_layers * n_qr)) / (qr_ms / 1e3) / 1e12
-        traffic, tsrc = traffic_record(["hqr_grid.cu"])
+        traffic, tsrc = traffic_record(["hqr_grid.cu"], sketch_elements(blog) / (K * n_layers * n_qr))
         roofline = {"bound": "alu", "kernel": "k_hqr_items: whole-GPU Householder QR (explicit Q) of the randomized "
                                               "range finder's sketches Y (m x l) and Z (n x l) of every bond of a layer",
                     "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
@@ -506,6 +527,8 @@ def run_ours(args, rank, world, local):
                       "l2": "flushed between timed steps (256 MiB write)",
                       "parallelism": f"{world} replicas" if world > 1 else "single GPU"},
            "clocks": clocks, "roofline": roofline, "e2e": e2e,
+           "routes": {layer: {"svd_pivoted_qr": r[0], "outer_block_qr": r[1], "tuned": r[2], "from_cache": r[3],
+                              "candidate_ms": r[4]} for layer, r in routes.items()},
            "gpu_launches": int(launches_per_step) * K,
            "gpu_launches_per_step": int(launches_per_step),
            "algorithmic_tflops": (fl_path + fl_rest) / (total_ms / 1e3) / 1e12,

@@ -83,6 +83,9 @@ typedef struct {
   const int* kappa0;              /* [N] initial augmented dims or NULL */
   const double* const* gamma0;    /* [N] pointers to Gamma_n[chi0[n]][4][kappa0[n]][chi0[n+1]] complex */
   const double* const* lambda0;   /* [N+1] pointers to real lambda_n[chi0[n]] */
+  const double* lognorm0;         /* with gamma0: [N+1] log-norms carried by the bonds (the state is
+                                     exp(their sum) times the network; a checkpoint's
+                                     pt_tebd_get_lognorms), or NULL for none */
 } pt_chain_desc;
 
 /* One PT-MPO (App. A.1; shared by every site whose bath is identical). */
@@ -163,15 +166,19 @@ int pt_tune_cache_store(const char* path, const char* key, int qr, int k2);
 int pt_tebd_get_dims(pt_tebd_t h, int chain, int* chi, int* kappa);
 int pt_tebd_get_lambda(pt_tebd_t h, int chain, int bond, double* out, int cap);
 int pt_tebd_get_lognorm(pt_tebd_t h, int chain, double* out);
+/* The same log-norm bond by bond: out[0..N] (their sum is pt_tebd_get_lognorm's value). */
+int pt_tebd_get_lognorms(pt_tebd_t h, int chain, double* out);
 
 /* Checkpoint read of one site tensor (App. B.2 continues a propagation from the full augmented MPS):
  * copies Gamma_n of `site` (0-based) of `chain` into out as complex [chi_{n-1}][4][kappa_n][chi_n]
  * (interleaved re, im; the live dims of pt_tebd_get_dims), the layout pt_chain_desc.gamma0 takes.
  * cap is out's size in complex elements; out may be NULL to ask for the size. Synchronous; returns
  * the element count, PT_ERR_ARG when cap is too small. Together with pt_tebd_get_lambda and
- * pt_tebd_get_lognorm it gives a resumable state: a new handle initialised with these tensors as
- * gamma0 / lambda0, the log-norm folded into one Gamma, and every PT-MPO cut at the current step
- * (its tensors from P^(k+1) on, kappa[0] = the site's current kappa) continues the same run. */
+ * pt_tebd_get_lognorms it gives a resumable state: a new handle initialised with these tensors as
+ * gamma0 / lambda0, the log-norms as lognorm0, and every PT-MPO cut at the current step (its tensors
+ * from P^(k+1) on, kappa[0] = the site's current kappa) continues the same run: bit for bit when the
+ * cut PT-MPOs keep their largest bond (the new handle then has the same capacities, kernel routes and
+ * sketch matrix). */
 int pt_tebd_get_gamma(pt_tebd_t h, int chain, int site, double* out, size_t cap);
 
 /* Jacobi sweeps of the most recent update of every bond (odd-layer bonds first, then even):

@@ -24,7 +24,7 @@ ERRORS = {-1: "PT_ERR_ARG", -2: "PT_ERR_OOM", -3: "PT_ERR_CAPACITY", -4: "PT_ERR
 EXPORTS = [
     "pt_tebd_set_allocator", "pt_tebd_init", "pt_tebd_set_observables", "pt_tebd_step",
     "pt_tebd_observe", "pt_tebd_read_history", "pt_tebd_apply_local", "pt_tebd_steps_done",
-    "pt_tebd_get_dims", "pt_tebd_get_lambda", "pt_tebd_get_lognorm", "pt_tebd_get_gamma", "pt_tebd_get_svd_sweeps",
+    "pt_tebd_get_dims", "pt_tebd_get_lambda", "pt_tebd_get_lognorm", "pt_tebd_get_lognorms", "pt_tebd_get_gamma", "pt_tebd_get_svd_sweeps",
     "pt_tebd_clone", "pt_tebd_read_bond_log", "pt_tebd_step_kernels", "pt_tebd_get_routes",
     "pt_tune_cache_lookup", "pt_tune_cache_store",
     "pt_tebd_sync", "pt_tebd_destroy", "pt_tebd_last_error", "pt_tebd_set_timing",
@@ -55,7 +55,7 @@ class ChainDesc(C.Structure):
     _fields_ = [("N", C.c_int), ("rho0", c_double_p), ("gates_q", c_double_p),
                 ("gates_h", c_double_p), ("local_prop", c_double_p), ("ptmpo_id", c_int_p),
                 ("chi0", c_int_p), ("kappa0", c_int_p), ("gamma0", C.POINTER(c_double_p)),
-                ("lambda0", C.POINTER(c_double_p))]
+                ("lambda0", C.POINTER(c_double_p)), ("lognorm0", c_double_p)]
 
 
 class MpoDesc(C.Structure):
@@ -96,6 +96,7 @@ lib.pt_tebd_get_dims.argtypes = [C.c_void_p, C.c_int, c_int_p, c_int_p]
 lib.pt_tebd_get_lambda.argtypes = [C.c_void_p, C.c_int, C.c_int, c_double_p, C.c_int]
 lib.pt_tebd_get_lognorm.argtypes = [C.c_void_p, C.c_int, c_double_p]
 lib.pt_tebd_get_gamma.argtypes = [C.c_void_p, C.c_int, C.c_int, c_double_p, C.c_size_t]
+lib.pt_tebd_get_lognorms.argtypes = [C.c_void_p, C.c_int, c_double_p]
 lib.pt_tebd_get_svd_sweeps.argtypes = [C.c_void_p, c_int_p, C.c_int]
 lib.pt_tebd_clone.argtypes = [C.c_void_p, C.POINTER(C.c_void_p)]
 lib.pt_tebd_read_bond_log.argtypes = [C.c_void_p, C.c_int, C.c_int, c_int_p, C.c_size_t]
@@ -222,6 +223,10 @@ class Engine:
                 d.kappa0 = kap0.ctypes.data_as(c_int_p)
                 d.gamma0 = gp
                 d.lambda0 = lp_
+                if ch.get("lognorm0") is not None:
+                    ln = np.ascontiguousarray(np.asarray(ch["lognorm0"], dtype=np.float64).reshape(N + 1))
+                    self._keep.append(ln)
+                    d.lognorm0 = _dptr(ln)
         mdescs = (MpoDesc * max(1, len(pt_mpos)))()
         for m, Ps in enumerate(pt_mpos):
             K = len(Ps)
@@ -324,7 +329,7 @@ class Engine:
 
     def checkpoint(self):
         """The full augmented MPS of every chain at the current step (App. B.2), on the host:
-        [{'step', 'chi', 'kappa', 'gamma': [N], 'lambda': [N + 1], 'lognorm'}]."""
+        [{'step', 'chi', 'kappa', 'gamma': [N], 'lambda': [N + 1], 'lognorm': [N + 1]}]."""
         step = self.steps_done()
         out = []
         for c in range(self.n_chains):
@@ -332,7 +337,13 @@ class Engine:
             out.append({"step": step, "chi": chi.copy(), "kappa": kap.copy(),
                         "gamma": [self.get_gamma(c, n) for n in range(self.N[c])],
                         "lambda": [self.get_lambda(c, b)[:int(chi[b])].copy() for b in range(self.N[c] + 1)],
-                        "lognorm": self.get_lognorm(c)})
+                        "lognorm": self.get_lognorms(c)})
+        return out
+
+    def get_lognorms(self, chain):
+        """pt_tebd_get_lognorms: the log-norm carried by each of the chain's N + 1 bonds."""
+        out = np.zeros(self.N[chain] + 1, dtype=np.float64)
+        _check(lib.pt_tebd_get_lognorms(self.h, int(chain), _dptr(out)), self.h)
         return out
 
     def get_svd_sweeps(self, cap=4096):
@@ -383,10 +394,10 @@ class Engine:
 
 def resume_problem(chains, pt_mpos, ckpt):
     """Inputs of pt_tebd_init that continue a run from a checkpoint (Engine.checkpoint) taken after
-    step s: every chain starts from its augmented MPS at step s, its log-norm folded into the first
-    site tensor (exp(lognorm) Gamma_1: the state, and so every raw Tr(O rho), is unchanged), and every
-    PT-MPO is cut to its tensors P^(s+1), ... (its bond kappa[s] becomes the first). History index 0
-    of the new handle is step s of the original run."""
+    step s: every chain starts from its augmented MPS and log-norm at step s, and every PT-MPO is cut
+    to its tensors P^(s+1), ... (its bond kappa[s] becomes the first). The new handle continues the
+    same run (bit for bit when the cut PT-MPOs keep their largest bond, so the new handle has the same
+    capacities); its history index 0 is step s of the original run."""
     steps = {int(ck["step"]) for ck in ckpt}
     if len(steps) != 1:
         raise ValueError("checkpoint chains are at different steps")
@@ -394,11 +405,11 @@ def resume_problem(chains, pt_mpos, ckpt):
     out = []
     for ch, ck in zip(chains, ckpt):
         d = dict(ch)
-        gam = [np.array(g, dtype=np.complex128) for g in ck["gamma"]]
-        gam[0] = gam[0] * np.exp(ck["lognorm"])
         d.update(rho0=None, chi0=np.asarray(ck["chi"], dtype=np.int32),
-                 kappa0=np.asarray(ck["kappa"], dtype=np.int32), gamma0=gam,
-                 lambda0=[np.asarray(l, dtype=np.float64) for l in ck["lambda"]])
+                 kappa0=np.asarray(ck["kappa"], dtype=np.int32),
+                 gamma0=[np.array(g, dtype=np.complex128) for g in ck["gamma"]],
+                 lambda0=[np.asarray(l, dtype=np.float64) for l in ck["lambda"]],
+                 lognorm0=np.asarray(ck["lognorm"], dtype=np.float64).copy())
         out.append(d)
     return out, [list(Ps[s:]) for Ps in pt_mpos]
 

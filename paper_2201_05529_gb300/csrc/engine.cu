@@ -36,6 +36,7 @@ struct HostChain {
   std::vector<int> chi0, kappa0;          // optional
   std::vector<std::vector<cplx>> gamma0;  // optional
   std::vector<std::vector<double>> lambda0;
+  std::vector<double> lognorm0;           // optional: initial log-norm of each bond (N+1)
 };
 
 struct HostMpo {
@@ -473,6 +474,11 @@ int copy_problem(pt_tebd* h, const pt_chain_desc* chains, int n_chains, const pt
     if (has_mps) {
       if (!d.chi0 || !d.kappa0 || !d.lambda0) return h->fail(PT_ERR_ARG, "gamma0 needs chi0, kappa0, lambda0");
       hc.chi0.assign(d.chi0, d.chi0 + d.N + 1);
+      if (d.lognorm0) {
+        hc.lognorm0.assign(d.lognorm0, d.lognorm0 + d.N + 1);
+        for (double x : hc.lognorm0)
+          if (!std::isfinite(x)) return h->fail(PT_ERR_ARG, "lognorm0 must be finite");
+      }
       hc.kappa0.assign(d.kappa0, d.kappa0 + d.N);
       if (hc.chi0[0] != 1 || hc.chi0[d.N] != 1) return h->fail(PT_ERR_ARG, "chi0 ends must be 1");
       for (int n = 0; n < d.N; ++n) {
@@ -661,6 +667,14 @@ int tune_layer(pt_tebd* h, const BondWork* work, int n, const std::vector<BondWo
 }
 
 // ---------------------------------------------------------------- initial state
+// the log-norm carried per bond (the state is exp(sum) times the network): zero, or the caller's
+std::vector<double> initial_lognorms(const pt_tebd* h) {
+  std::vector<double> v(h->n_lams, 0.0);
+  for (int c = 0; c < (int)h->chains.size(); ++c)
+    for (size_t b = 0; b < h->chains[c].lognorm0.size(); ++b) v[h->lam0[c] + b] = h->chains[c].lognorm0[b];
+  return v;
+}
+
 // Gamma and lambda of the initial augmented MPS (product state or the caller's gamma0/lambda0)
 void upload_initial_gamma_lambda(pt_tebd* h) {
   for (int c = 0; c < (int)h->chains.size(); ++c) {
@@ -728,7 +742,11 @@ int choose_routes(pt_tebd* h, const std::vector<BondWork>& odd, const std::vecto
   upload_initial_gamma_lambda(h);
   cudaMemcpyAsync(T.site_kappa, h->kap_init_h.data(), sizeof(int) * h->n_sites, cudaMemcpyHostToDevice, h->stream);
   cudaMemcpyAsync(T.lam_chi, h->chi_init_h.data(), sizeof(int) * h->n_lams, cudaMemcpyHostToDevice, h->stream);
-  cudaMemsetAsync(T.lam_lognorm, 0, sizeof(double) * h->n_lams, h->stream);
+  {
+    const std::vector<double> ln = initial_lognorms(h);
+    cudaMemcpyAsync(T.lam_lognorm, ln.data(), sizeof(double) * h->n_lams, cudaMemcpyHostToDevice, h->stream);
+    cudaStreamSynchronize(h->stream);     // ln is a local host buffer
+  }
   cudaMemsetAsync(T.step, 0, sizeof(int), h->stream);
   cudaMemsetAsync(T.status, 0, sizeof(int), h->stream);
   return rc != PT_OK ? rc : check_cuda(h, "autotune restore");
@@ -899,8 +917,7 @@ int build(pt_tebd* h) {
   T.lam_ptr = upload(h, h->lam_buf);
   T.lam_chi = upload(h, chi_init);
   T.lam_cap = upload(h, h->lam_cap_h);
-  std::vector<double> zeros(h->n_lams, 0.0);
-  T.lam_lognorm = upload(h, zeros);
+  T.lam_lognorm = upload(h, initial_lognorms(h));
   std::vector<int> Nv(C);
   for (int c = 0; c < C; ++c) Nv[c] = h->chains[c].N;
   T.chain_site0 = upload(h, h->site0);
@@ -1508,6 +1525,14 @@ int pt_tebd_get_lognorm(pt_tebd_t h, int chain, double* out) {
   for (double x : v) s += x;
   *out = s;
   return rc;
+}
+
+int pt_tebd_get_lognorms(pt_tebd_t h, int chain, double* out) {
+  if (!h || chain < 0 || chain >= h->n_chains || !out) return PT_ERR_ARG;
+  const int N = h->chains[chain].N;
+  cudaMemcpyAsync(out, h->T.lam_lognorm + h->lam0[chain], sizeof(double) * (N + 1), cudaMemcpyDeviceToHost,
+                  h->stream);
+  return read_status(h);
 }
 
 int pt_tebd_get_gamma(pt_tebd_t h, int chain, int site, double* out, size_t cap) {

@@ -49,7 +49,7 @@ def test_svd_scratch_size_is_positive(capi):
     assert capi.svd_scratch_bytes(0, 4, 1) == 0
 
 
-def test_resume_problem_cuts_the_pt_mpos_and_folds_the_log_norm(capi):
+def test_resume_problem_cuts_the_pt_mpos_and_carries_the_log_norm(capi):
     import numpy as np
     rng = np.random.default_rng(3)
     chis, kaps = [1, 2, 3, 1], [2, 1, 3]
@@ -59,12 +59,12 @@ def test_resume_problem_cuts_the_pt_mpos_and_folds_the_log_norm(capi):
     Q = [rng.normal(size=(1 if k == 0 else 3, 4, 4, 3)) + 0j for k in range(6)]
     chains = [dict(N=3, rho0=np.zeros((3, 4)), gates_q=np.zeros((2, 16, 16)), gates_h=np.zeros((2, 16, 16)),
                    ptmpo_id=[0, -1, 1])]
-    ck = [{"step": 4, "chi": np.array(chis), "kappa": np.array(kaps), "gamma": gam, "lambda": lam, "lognorm": -0.75}]
+    ck = [{"step": 4, "chi": np.array(chis), "kappa": np.array(kaps), "gamma": gam, "lambda": lam, "lognorm": np.array([-0.75, 0.25, 0.0, 0.5])}]
     rc, rm = capi.resume_problem(chains, [P, Q], ck)
     assert [len(x) for x in rm] == [2, 2] and rm[0][0] is P[4] and rm[1][1] is Q[5]
     d = rc[0]
     assert d["rho0"] is None and list(d["chi0"]) == chis and list(d["kappa0"]) == kaps
-    assert np.allclose(d["gamma0"][0], gam[0] * np.exp(-0.75)) and d["gamma0"][1] is not gam[1]
+    assert np.array_equal(d["gamma0"][0], gam[0]) and d["gamma0"][1] is not gam[1] and list(d["lognorm0"]) == [-0.75, 0.25, 0.0, 0.5]
     assert np.array_equal(d["gamma0"][2], gam[2]) and d["ptmpo_id"] == [0, -1, 1]
     assert chains[0]["rho0"] is not None                   # the caller's dicts are not modified
     with pytest.raises(ValueError):

@@ -1,15 +1,16 @@
 """Checkpoint and resume (App. B.2: the propagation continues from the full augmented MPS).
 
 A run of the five-site two-bath chain is stopped after step s, its state read to the host
-(pt_tebd_get_gamma, pt_tebd_get_lambda, pt_tebd_get_lognorm), and a new handle is initialised from
-those host buffers with every PT-MPO cut at step s. The resumed run must reproduce the continuous
-run's observables, trace and bond dimensions step by step, and stay within the FP64 bar of the
-oracle. The steps stay inside the window where the oracle's own rounding envelope is below 1e-9."""
+(pt_tebd_get_gamma, pt_tebd_get_lambda, pt_tebd_get_lognorms), and a new handle is initialised
+from those host buffers with every PT-MPO cut at step s. The resumed run must reproduce the
+continuous run's observables, trace and bond dimensions (to 1e-12; bit for bit when the new
+handle's capacities match), and stay within the FP64 bar of the oracle. The steps stay inside the
+window where the oracle's own rounding envelope is below 1e-9."""
 import numpy as np
 import pytest
 
 from workloads import workload
-from oracle import model, problem as oprob
+from oracle import problem as oprob
 from tests.gpu_helpers import OPS, engine_args_from_oracle, run_oracle
 
 pytestmark = pytest.mark.gpu
@@ -27,8 +28,8 @@ def capi():
     return c
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("bf16_ozaki", 1e-8)])
-def test_resume_from_host_checkpoint(capi, precision, tol):
+@pytest.mark.parametrize("precision", ["fp64", "bf16_ozaki"])
+def test_resume_from_host_checkpoint(capi, precision):
     S, K = 5, 12
     w = workload("xyz5_twobaths", K=K)
     cis = oprob.build_inputs(w)
@@ -61,8 +62,13 @@ def test_resume_from_host_checkpoint(capi, precision, tol):
     dims_r = res.get_dims(0)
     res.destroy()
 
-    assert np.max(np.abs(obs_r - obs_full[S:])) < tol
-    assert np.max(np.abs(tr_r - tr_full[S:])) < tol
+    # the same tensors, per-bond log-norms and kernels: the continuation is the same run (bit for bit
+    # when the new handle's capacities, and so its kernel routes, match; held here to 1e-12)
+    d_obs = float(np.max(np.abs(obs_r - obs_full[S:])))
+    d_tr = float(np.max(np.abs(tr_r - tr_full[S:])))
+    print(f"resume ({precision}): max |obs - continuous| = {d_obs:.3e}, max |trace - continuous| = {d_tr:.3e}, "
+          f"bitwise: {np.array_equal(obs_r, obs_full[S:]) and np.array_equal(tr_r, tr_full[S:])}")
+    assert d_obs <= 1e-12 and d_tr <= 1e-12
     assert np.array_equal(dims_r[0], dims_full[0]) and np.array_equal(dims_r[1], dims_full[1])
     if precision == "fp64":
         ref = run_oracle(w, cis, OPS, K=K)[0]
