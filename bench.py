@@ -298,6 +298,29 @@ def _secondary(capi, pp, workload, torch, stream, flush, prec, W=5, K=20):
     return out
 
 
+def _stress(capi, pp, workload, torch, stream, flush, prec, W=1, K=2):
+    """The random augmented-MPS stress workload at full size (N = 32, chi = 96, kappa = 16 on every
+    site: D up to 1536 x 1536), the fast path only (the FP64 path's exact Jacobi on full-rank D of
+    that size runs minutes per step)."""
+    w = workload("random32_stress")
+    out = {"workload": w.name, "precision": prec, "window": f"steps {W}..{W + K} of {w.K}"}
+    try:
+        chains, mpos = pp.build_problem(w)
+        N = sum(c["N"] for c in chains)
+        e = capi.Engine(chains, mpos, chi_max=w.chi_max, eps=w.eps, precision=prec, multiplet_tol=w.multiplet_tol,
+                        max_steps=w.K, use_graph=True)
+        e.set_observables([pp.pauli("z")])
+        e.step(W)
+        ms = _timed_window(e, K, stream, flush, torch)
+        blog, _ = e.read_bond_log(W, K)
+        e.destroy()
+        out.update(value=N * K / (sum(ms) / 1e3), ms_per_step=float(np.mean(ms)),
+                   max_D=[int(blog[..., 0].max()), int(blog[..., 1].max())])
+    except Exception as ex:          # reported, not fatal
+        out["error"] = str(ex)[:300]
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2201_05529_gb300 as pkg
@@ -538,6 +561,8 @@ def run_ours(args, rank, world, local):
         out["speedup_vs_fp64_path"] = value / fp64["value"]
     if not args.no_secondary and args.workload != SECONDARY_WORKLOAD:
         out["secondary"] = _secondary(capi, pp, workload, torch, stream, flush, args.precision)
+        if args.precision == "bf16_ozaki":
+            out["stress"] = _stress(capi, pp, workload, torch, stream, flush, args.precision)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, W, K)
     if world > 1:

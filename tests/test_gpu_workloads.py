@@ -147,6 +147,39 @@ def test_random_stress_state_singular_values():
     eng.destroy()
 
 
+def test_random_stress_full_size_first_step_fast_path():
+    # the stress workload at full size (N = 32, chi = 96, kappa = 16 on every site: D up to
+    # 1536 x 1536) on the fast path, one step, against the oracle's state after that step
+    # (tests/golden/random32_step1.json, written by tests/golden/make_random32_step1.py from the
+    # oracle alone). Checked: every bond update ran at full size without a fault flag, the bond
+    # dimensions equal the oracle's, and the singular values agree to what a randomized range finder
+    # can give on this state. Its D have flat spectra (on bond 2 of the first layer
+    # sigma_96 / sigma_1 = 0.38 and sigma_129 / sigma_96 = 0.83, so the range finder's subspace
+    # error at the cut, (sigma_{l+1} / sigma_chi)^(2q+1) with l = 128, q = 2, is ~0.4): a CPU run of
+    # the same algorithm in FP64 on that D leaves the normalised singular values 1.6e-3 off, and the
+    # step has six layers. The random state's raw Tr(O rho) underflows to 0 (its caps shrink ~1e-11
+    # per site), so observables carry no information here. The FP64 path's exact Jacobi on
+    # full-rank D of this size runs minutes per step and is not run.
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "random32_step1.json")))
+    w = workload("random32_stress")
+    assert g["K"] == w.K and g["chi_max"] == w.chi_max
+    cis = oprob.build_inputs(w)
+    eng, obs, tr = run_gpu(w, cis, [model.SZ, model.SX], K=1, precision="bf16_ozaki")
+    chi, kap = eng.get_dims(0)
+    lam_err = max(float(np.max(np.abs(eng.get_lambda(0, b) - np.array(g["lambda"][b])))) for b in range(1, 32))
+    blog, _ = eng.read_bond_log(0, 1)
+    eng.destroy()
+    print(f"random32 full size, fast path, step 1: D up to {blog[..., 0].max()} x {blog[..., 1].max()}, "
+          f"max |lambda - oracle| = {lam_err:.2e}")
+    assert int(blog[..., 0].max()) == 1536 and int(blog[..., 1].max()) == 1536
+    assert not np.any(blog[..., 4])                      # no fault flags
+    assert list(chi) == g["chis"] and list(kap) == g["kappas"]
+    assert lam_err < 5e-2
+    assert np.all(np.isfinite(obs)) and np.all(np.isfinite(tr))
+
+
 @pytest.fixture(scope="module")
 def xy21_ten_steps():
     # the 21-site workload itself, first 10 steps (chi reaches ~85, D up to ~1300 x 1300): the oracle
