@@ -4,9 +4,9 @@
  * PT-TEBD (arXiv:2201.05529) evolves chains of open quantum systems in Liouville space: an
  * augmented MPS in Vidal form, Gamma_n[chi_{n-1}][d^2][kappa_n][chi_n] and lambda_n[chi_n]
  * (App. A.1), is advanced per time step by the second-order splitting of Eq. (propagator-env):
- * a chain half step, the PT-MPO site contractions (App. A.2, (i-j)), and another chain half step,
+ * a chain half step, the PT-MPO site contractions (App. A.2), and another chain half step,
  * each chain half being O(dt/4) E(dt/2) O(dt/4) layers of two-site Liouville gates applied by
- * the contraction/decomposition sequence (c-h) of App. A.2 with exact QR reductions and an FP64
+ * the contraction/decomposition sequence of App. A.2 with exact QR reductions and an FP64
  * one-sided Jacobi SVD truncated by the relative rule of App. A.2. Observables are read out by
  * closing the augmented legs with cap tensors (App. A.3) and the Liouville legs with trace or
  * observable vectors; two-time correlations insert a left/right super-operator (App. A.4).
@@ -219,7 +219,7 @@ int pt_tebd_get_timing(pt_tebd_t h, double* ms9);
 
 /* ---- kernel-level entry points (single operations on device buffers, for unit tests) ---- */
 
-/* Batched FP64 SVD (the one-sided Jacobi of the bond update, App. A.2 (f-g)) of `batch` complex
+/* Batched FP64 SVD (the one-sided Jacobi of the bond update, App. A.2) of `batch` complex
  * matrices A_b [m][n] row-major (device). Writes singular values sigma [batch][min(m,n)]
  * (descending), U [batch][m][min(m,n)] and V [batch][n][min(m,n)] (device, row-major), so
  * A_b = U diag(sigma) V^H. scratch: device workspace of pt_svd_scratch_bytes(m, n, batch) bytes.
@@ -229,7 +229,7 @@ int pt_svd_f64(const double* A, int m, int n, int batch, double* sigma, double* 
                void* scratch, int max_sweeps, void* cuda_stream);
 
 /* Batched FP64 Householder QR with the explicit Q (the whole-GPU kernel of the outer-block
- * reductions, App. A.2 (d-e), and of the fast path's range finder): A_b (m x n complex,
+ * reductions, App. A.2, and of the fast path's range finder): A_b (m x n complex,
  * column-major, 1 <= n <= m, b < batch, contiguous) is replaced by Q_b (m x n, orthonormal columns),
  * R_b (n x n, column-major, upper triangular) is written, A_b(in) = Q_b R_b. scratch: device workspace
  * of pt_qr_scratch_bytes(m, n, batch) bytes. Synchronous. Errors: PT_ERR_ARG, PT_ERR_CAPACITY
@@ -238,7 +238,7 @@ size_t pt_qr_scratch_bytes(int m, int n, int batch);
 int pt_qr_f64(double* A, int m, int n, int batch, double* R, void* scratch, void* cuda_stream);
 
 /* Batched complex GEMM of the fast path on the tensor cores (the products of the fast path's bond
- * SVD, App. A.2 (f)): C_b = opA(A_b) opB(B_b), b < batch, C_b m x n, inner dimension k. Every
+ * SVD, App. A.2): C_b = opA(A_b) opB(B_b), b < batch, C_b m x n, inner dimension k. Every
  * matrix is complex double (interleaved re, im), column-major, with the given leading dimension
  * (in complex elements) and batch stride (in complex elements); op: 0 as stored, 1 transposed,
  * 2 conjugate transposed. Arithmetic: each row of opA(A) and column of opB(B) is scaled by a power

@@ -89,7 +89,7 @@ struct Tables {
   int* status;             // [1] device status word (ST_* bits)
 };
 
-// One two-site bond update (App. A.2 (c-h)) with its private scratch.
+// One two-site bond update (App. A.2) with its private scratch.
 struct BondWork {
   int chain;
   int site_l;              // global index of the left site

@@ -1,4 +1,4 @@
-// Cluster-parallel one-sided Jacobi SVD (App. A.2 (f-g): the SVD of D).
+// Cluster-parallel one-sided Jacobi SVD (App. A.2: the SVD of D).
 //
 // One thread-block cluster (up to 16 CTAs of 1024 threads) works on one matrix held column-major
 // in global memory (L2-resident at these sizes). Each round of the round-robin tournament is a set

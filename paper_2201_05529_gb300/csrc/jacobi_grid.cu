@@ -1,4 +1,4 @@
-// Whole-GPU one-sided Jacobi SVD for all bond matrices of one layer (App. A.2 (f-g)).
+// Whole-GPU one-sided Jacobi SVD for all bond matrices of one layer (App. A.2).
 //
 // The SVD is bound by FP64 arithmetic (1.2 TFLOP/s on GB300, ~7.9 GFLOP/s per SM), so every SM
 // must work on it even when a layer has only two bonds. One cooperative launch (one 512-thread

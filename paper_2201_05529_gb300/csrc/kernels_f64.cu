@@ -35,7 +35,7 @@ PT_DEV double block_sum(double v, double* red) {
 }
 
 // ------------------------------------------------------------------ K1: PT site contraction
-// App. A.2 (i-j): Gamma'[l,p',b,r] = sum_{a,p} Gamma[l,p,a,r] P^(k)[a,p,p',b] with k = step+1.
+// App. A.2: Gamma'[l,p',b,r] = sum_{a,p} Gamma[l,p,a,r] P^(k)[a,p,p',b] with k = step+1.
 __global__ void k_site_contract(Tables T, const SiteWork* work, int n_work) {
   const int w = blockIdx.y;
   if (w >= n_work) return;
@@ -87,7 +87,7 @@ __global__ void k_site_swap(Tables T, const SiteWork* work, int n_work) {
 }
 
 // ------------------------------------------------------------------ K2a: B_L and B_R^H
-// App. A.2 (c-d): B_L = lambda_{n-1} Gamma_n as [(l,a),(p,c)], B_R = Gamma_{n+1} lambda_{n+1} as
+// App. A.2: B_L = lambda_{n-1} Gamma_n as [(l,a),(p,c)], B_R = Gamma_{n+1} lambda_{n+1} as
 // [(c,q),(b,r)]. B_L is stored column-major in QL; B_R^H column-major in QR.
 __global__ void k_build_blocks(Tables T, const BondWork* work, int n_work) {
   const int w = blockIdx.y;
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_householder(Tables T, const Bond
 }
 
 // ------------------------------------------------------------------ K3: theta + gate
-// App. A.2 (e-f): D[(u,p'),(q',v)] = sum_{pq} G[p'q',pq] sum_c R_L[u,(p,c)] lambda_c L_R[(c,q),v].
+// App. A.2: D[(u,p'),(q',v)] = sum_{pq} G[p'q',pq] sum_c R_L[u,(p,c)] lambda_c L_R[(c,q),v].
 // D (m >= n) or D^H (m < n) is written column-major into W.A for the one-sided Jacobi.
 __global__ void k_theta_gate(Tables T, const BondWork* work, int n_work) {
   const int w = blockIdx.y;
@@ -421,7 +421,7 @@ __global__ void k_tune_fill(Tables T, int n_sites, int n_lams, unsigned seed) {
 }
 
 // ------------------------------------------------------------------ K6: Gamma recovery
-// App. A.2 (g-h): Gamma_L = lambda_{n-1}^{-1} Q_L U, Gamma_R = V^H Q_R lambda_{n+1}^{-1}.
+// App. A.2: Gamma_L = lambda_{n-1}^{-1} Q_L U, Gamma_R = V^H Q_R lambda_{n+1}^{-1}.
 __global__ void k_recover(Tables T, const BondWork* work, int n_work) {
   const int w = blockIdx.y;
   if (w >= n_work) return;

@@ -1,4 +1,4 @@
-// QR-preconditioned one-sided Jacobi for the bond SVD (App. A.2 (f-g)).
+// QR-preconditioned one-sided Jacobi for the bond SVD (App. A.2).
 //
 // A one-sided Jacobi on a rank-deficient, strongly graded D needs many sweeps (17-23 on the
 // five-site chain's 256x256 blocks); after a column-pivoted QR, D P = Q R, the same Jacobi on R^H

@@ -1,4 +1,4 @@
-// The fast path's bond SVD as a randomized truncated SVD (App. A.2 (f)): the SVD of D only has to
+// The fast path's bond SVD as a randomized truncated SVD (App. A.2): the SVD of D only has to
 // deliver the chi <= chi_max leading singular triplets and the norm of everything it discards, so
 // the fast path finds them in an l-dimensional subspace, l = min(n, chi_max + p), p = 32 extra
 // directions (Halko, Martinsson and Tropp's range finder with q = RSVD_POWER power iterations):

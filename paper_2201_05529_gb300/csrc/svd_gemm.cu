@@ -1,4 +1,4 @@
-// FP64 GEMM of the SVD's finish (App. A.2 (f-g)): U_D = D V_D on the columns the truncation keeps,
+// FP64 GEMM of the SVD's finish (App. A.2): U_D = D V_D on the columns the truncation keeps,
 // batched over the bonds of a layer with each bond's live dims read from its info words.
 #include "kernels.h"
 

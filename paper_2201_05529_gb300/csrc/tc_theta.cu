@@ -1,4 +1,4 @@
-// Tensor-core theta + gate of the fast path (App. A.2 (e-f)) on sm_103a: tcgen05 + TMEM.
+// Tensor-core theta + gate of the fast path (App. A.2) on sm_103a: tcgen05 + TMEM.
 //
 // The two-site gate acts on the Liouville legs p (left) and q (right) of
 //   theta[(u,p),(q,v)] = sum_c R_L[u,(p,c)] lambda_c L_R[(c,q),v],

@@ -1,5 +1,5 @@
 // Batched complex GEMM on the tensor cores with an FP64-class result, for the large products of
-// the fast path's bond SVD (App. A.2 (f)): the randomized range finder's sketches D Omega and
+// the fast path's bond SVD (App. A.2): the randomized range finder's sketches D Omega and
 // D^H Q, the projection Q^H D, and the singular vectors of D built from those of the small factor.
 //
 //   C_i = opA(A_i) opB(B_i)        (M_i x N_i, inner dimension K_i; op = as stored, T or H)

@@ -65,7 +65,7 @@ def oracle_envelope(w, ci, ops, K=None, scale=1e-13, seed=1, insert=None):
     `scale` relative noise on the dt/4 gates)| per step, as a running maximum over steps.
 
     Once the chi cap binds, the kept singular values reach ~1e-9 of the largest and the lambda^-1
-    of the Gamma recovery (App. A.2 (g-h)) amplifies rounding differences step by step, up to the
+    of the Gamma recovery (App. A.2) amplifies rounding differences step by step, up to the
     accumulated truncation error; two correct FP64 implementations can then differ by this much.
     """
     rng = np.random.default_rng(seed)

@@ -3,7 +3,7 @@
 Tolerance (FP64 path): 1e-9 absolute on every observable at every step, the bar the PT-TEBD
 target sets for the FP64 GPU path; bond dimensions must agree exactly and singular values to 1e-9.
 Where the chi cap binds, the truncated trajectory amplifies rounding differences (the lambda^-1 of
-App. A.2 (g-h) on singular values down to ~1e-9 of the largest), so there the bar is
+App. A.2 on singular values down to ~1e-9 of the largest), so there the bar is
 1e-9 + 10 x the oracle's own sensitivity to a 1e-13 relative perturbation of its gates, measured
 per step on the same inputs (``oracle_envelope``).
 """
@@ -115,7 +115,7 @@ def test_two_time_correlation_five_sites():
 
 def test_qr_reduced_path_all_sites_with_baths():
     # every site has a bath: B_L is taller than wide and B_R wider than tall, so both the QR and
-    # the LQ reductions of App. A.2 (d-e) run
+    # the LQ reductions of App. A.2 run
     b = BathSpec(0.05, 3.0, 0.8)
     ch = ChainSpec(N=5, eps=(0.0,) * 5, J=((1.0, 1.0, 0.0),) * 4, init="ddudd", baths=(b,) * 5)
     w = Workload("t", (ch,), dt=0.1, K=8, chi_max=48, eps=1e-8, kappa_max=6)

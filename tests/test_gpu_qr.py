@@ -1,4 +1,4 @@
-"""The whole-GPU Householder QR (explicit Q) of the outer-block reductions (App. A.2 (d-e)) and of the
+"""The whole-GPU Householder QR (explicit Q) of the outer-block reductions (App. A.2) and of the
 fast path's range finder, through pt_qr_f64, against the definition: A = Q R with orthonormal Q and
 upper-triangular R, to FP64 accuracy (|A - QR| and |Q^H Q - I| within 1e-13 x m of the scale).
 Shapes: single columns, square, tall, tiny blocks of the outer reductions (6 x 4), sizes spanning

@@ -42,7 +42,7 @@ def test_markovian_limit_converges_to_expm_at_second_order(N):
 
 
 def test_qr_and_svd_reductions_agree_without_truncation():
-    # The paper's (d-e) truncated SVDs and the exact QR reductions give the same D up to a unitary
+    # The paper's truncated SVDs of the outer blocks and the exact QR reductions give the same D up to a unitary
     # change of basis, hence the same singular values and observables when nothing is truncated.
     w = workload("xyz3_onebath", K=8, kappa_max=64, eps=1e-13)
     ci = problem.build_inputs(w)[0]
