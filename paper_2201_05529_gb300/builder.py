@@ -58,7 +58,7 @@ def build(verbose=False, force=False):
         list(ex.map(run, jobs))
     if jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 #include "../../include/pt_tebd.h"
 
@@ -26,6 +28,15 @@ pt_alloc_fn g_alloc = nullptr;
 pt_free_fn g_free = nullptr;
 void* g_ctx = nullptr;
 thread_local std::string g_err;
+
+// NVTX range over a host scope (a tracing tool, when one is attached, sees the step's stages and the
+// kernel launches inside them; without a tool the calls do nothing)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct HostChain {
   int N;
@@ -259,6 +270,7 @@ constexpr double FAST_MULTIPLET_TOL = 1e-9;
 
 void enqueue_layer(pt_tebd* h, const BondWork* work, int n, int layer) {
   if (n == 0) return;
+  NvtxRange nv(work == h->d_odd ? "pt_tebd bond layer (odd bonds)" : "pt_tebd bond layer (even bonds)");
   cudaStream_t s = h->stream;
   cudaEvent_t e = nullptr;
   ev_begin(h, 1, &e);
@@ -376,6 +388,7 @@ void enqueue_chain_half(pt_tebd* h, int first_layer) {
 
 void enqueue_observe_history(pt_tebd* h) {
   if (h->n_ops == 0) return;
+  NvtxRange nv("pt_tebd readout");
   cudaEvent_t e = nullptr;
   ev_begin(h, 6, &e);
   ptk::k_observe_m<<<dim3(h->gx_m, h->n_chains, h->n_max), 256, 0, h->stream>>>(h->T, h->n_chains, h->d_Mbuf,
@@ -389,6 +402,7 @@ void enqueue_observe_history(pt_tebd* h) {
 void enqueue_step(pt_tebd* h) {
   enqueue_chain_half(h, 0);
   if (h->n_site_work > 0) {
+    NvtxRange nv("pt_tebd site layer");
     cudaEvent_t e = nullptr;
     ev_begin(h, 0, &e);
     if (h->d_site_items)
@@ -1292,6 +1306,7 @@ int pt_tebd_init(pt_tebd_t* out, const pt_chain_desc* chains, int n_chains, cons
     return PT_ERR_ARG;
   }
   *out = nullptr;
+  NvtxRange nv("pt_tebd_init");
   pt_tebd* h = new pt_tebd();
   h->stream = (cudaStream_t)cuda_stream;
   h->opt = *opt;
@@ -1351,6 +1366,7 @@ int pt_tebd_step(pt_tebd_t h, int n_steps) {
   if (h->steps_done + n_steps > h->K_limit)
     return h->fail(PT_ERR_STEPS, "step: past the end of the PT-MPOs / history capacity");
   h->ev_used = 0;
+  NvtxRange nv("pt_tebd_step");
   for (int i = 0; i < n_steps; ++i) {
     if (h->graph && !h->timing) {
       if (cudaGraphLaunch(h->graph, h->stream) != cudaSuccess) return check_cuda(h, "graph launch");
