@@ -319,7 +319,7 @@ void enqueue_layer(pt_tebd* h, const BondWork* work, int n, int layer) {
     gemm(L.gz2, lc);                                    // Z = D^H Q = B^H
     gemm(L.gres, mc);                                   // D - Q Z^H
     ev_begin(h, 8, &e);
-    ptk::launch_rsvd_tail_norm(work, n, s);
+    ptk::launch_rsvd_tail_norm(work, n, L.fro_part, s);
     ev_end(h, e);
     qr(L.qb);                                           // Z = Qb Rb
     ev_begin(h, 3, &e);
@@ -1124,7 +1124,8 @@ int build(pt_tebd* h) {
       for (auto p : z) *p = (ptk::ZGemmItem*)h->dalloc(sizeof(ptk::ZGemmItem) * n);
       ptk::QRItem** q[4] = {&L.q1, &L.qz, &L.q2, &L.qb};
       for (auto p : q) *p = (ptk::QRItem*)h->dalloc(sizeof(ptk::QRItem) * n);
-      bool ok = true;
+      L.fro_part = (double*)h->dalloc(sizeof(double) * n * ptk::RSVD_FRO_PARTS);
+      bool ok = L.fro_part != nullptr;
       for (auto p : z) ok = ok && *p;
       for (auto p : q) ok = ok && *p;
       return ok && cols <= (long long)h->grid_blocks * 384;

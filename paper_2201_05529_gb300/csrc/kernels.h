@@ -145,6 +145,7 @@ void launch_recover_tc(const Tables& T, const BondWork* work, int n_work, ZGemmI
 struct RsvdLists {
   ZGemmItem *gy1, *gz1, *gy2, *gz2, *gres, *gu, *gv;
   QRItem *q1, *qz, *q2, *qb;
+  double* fro_part;        // RSVD_FRO_PARTS doubles per bond: partial sums of the tail norm
   int tile_cap;            // output tiles of one product over the layer at capacity
   int m_cap, l_cap;        // largest row count and range-finder width of the layer's bonds
 };
@@ -157,7 +158,9 @@ void launch_rsvd_omega(double2* Om, int rows, int cols, unsigned seed, cudaStrea
 // Jacobi on it (launch_jacobi_grid, on_b = 2); truncation (k_truncate, rsvd = 1); vectors
 void launch_rsvd_plan(const Tables& T, const BondWork* work, int n_work, const RsvdLists& L, int chi_max, int p,
                       const double2* Om, int ld_om, cudaStream_t st);
-void launch_rsvd_tail_norm(const BondWork* work, int n_work, cudaStream_t st);
+// part: RSVD_FRO_PARTS doubles per bond (scratch of the two-pass, fixed-order sum)
+constexpr int RSVD_FRO_PARTS = 64;
+void launch_rsvd_tail_norm(const BondWork* work, int n_work, double* part, cudaStream_t st);
 void launch_rsvd_vectors(const Tables& T, const BondWork* work, int n_work, const RsvdLists& L, cudaStream_t st);
 
 // set the message returned by pt_tebd_last_error(NULL) (engine.cu)

@@ -110,16 +110,20 @@ __global__ void k_rsvd_plan(const BondWork* work, int n_work, int chi_max, int p
 }
 
 // ||A||_F^2 of every bond's A (after the residual step: ||D - Q Q^H D||_F^2) into info[12..13]
-// (a double); one block per bond
-__global__ void k_rsvd_fro(const BondWork* work, int n_work) {
-  const int w = blockIdx.x;
+// (a double), in two passes with a fixed summation order (the result is reproducible bit for bit):
+// block p of bond w sums the p-th of RSVD_FRO_PARTS contiguous chunks of A into part[w][p], then
+// one block per bond adds the parts.
+__global__ void k_rsvd_fro_part(const BondWork* work, int n_work, double* part) {
+  const int w = blockIdx.y, p = blockIdx.x;
   if (w >= n_work) return;
   const BondWork& W = work[w];
   int Ma, Na;
   live_shape(W, &Ma, &Na);
   const size_t tot = (size_t)Ma * Na;
+  const size_t chunk = (tot + RSVD_FRO_PARTS - 1) / RSVD_FRO_PARTS;
+  const size_t lo = min(tot, (size_t)p * chunk), hi = min(tot, lo + chunk);
   double s = 0.0;
-  for (size_t i = threadIdx.x; i < tot; i += blockDim.x) {
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const double2 v = W.A[i];
     s = fma(v.x, v.x, fma(v.y, v.y, s));
   }
@@ -130,7 +134,20 @@ __global__ void k_rsvd_fro(const BondWork* work, int n_work) {
     if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *(double*)(W.info + 12) = red[0];
+  if (threadIdx.x == 0) part[(size_t)w * RSVD_FRO_PARTS + p] = red[0];
+}
+
+__global__ void k_rsvd_fro_sum(const BondWork* work, int n_work, const double* part) {
+  const int w = blockIdx.x;
+  if (w >= n_work) return;
+  __shared__ double red[RSVD_FRO_PARTS];
+  red[threadIdx.x] = part[(size_t)w * RSVD_FRO_PARTS + threadIdx.x];
+  __syncthreads();
+  for (int o = RSVD_FRO_PARTS / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *(double*)(work[w].info + 12) = red[0];
 }
 
 // After the truncation: the kept left vectors U_D[:, c] = Q Wr[:, perm[c]] (into A) and right
@@ -168,8 +185,9 @@ void launch_rsvd_plan(const Tables& T, const BondWork* work, int n_work, const R
                                                      L.gres, L.q1, L.qz, L.q2, L.qb, T.status);
 }
 
-void launch_rsvd_tail_norm(const BondWork* work, int n_work, cudaStream_t st) {
-  k_rsvd_fro<<<n_work, 256, 0, st>>>(work, n_work);
+void launch_rsvd_tail_norm(const BondWork* work, int n_work, double* part, cudaStream_t st) {
+  k_rsvd_fro_part<<<dim3(RSVD_FRO_PARTS, n_work), 256, 0, st>>>(work, n_work, part);
+  k_rsvd_fro_sum<<<n_work, RSVD_FRO_PARTS, 0, st>>>(work, n_work, part);
 }
 
 void launch_rsvd_vectors(const Tables& T, const BondWork* work, int n_work, const RsvdLists& L, cudaStream_t st) {
