@@ -163,10 +163,15 @@ int pt_tebd_get_routes(pt_tebd_t h, int* out8, float* ms10);
  * needed. */
 int pt_tune_cache_lookup(const char* path, const char* key, int* qr, int* k2);
 int pt_tune_cache_store(const char* path, const char* key, int qr, int k2);
+/* State of one chain (App. A.1's augmented MPS), synchronous, host outputs owned by the caller; each
+ * call also reports a pending device status error. get_dims: chi[0..N] bond dimensions and
+ * kappa[0..N-1] augmented dimensions (either may be NULL). get_lambda: the weights of bond `bond`
+ * (0..N) into out[0 .. min(chi, cap)), returns chi. get_lognorm: *out = the log-norm the chain has
+ * accumulated (the state is exp(*out) times the network); get_lognorms: the same bond by bond,
+ * out[0..N] (their sum is get_lognorm's value). PT_ERR_ARG for a bad chain, bond or NULL out. */
 int pt_tebd_get_dims(pt_tebd_t h, int chain, int* chi, int* kappa);
 int pt_tebd_get_lambda(pt_tebd_t h, int chain, int bond, double* out, int cap);
 int pt_tebd_get_lognorm(pt_tebd_t h, int chain, double* out);
-/* The same log-norm bond by bond: out[0..N] (their sum is pt_tebd_get_lognorm's value). */
 int pt_tebd_get_lognorms(pt_tebd_t h, int chain, double* out);
 
 /* Checkpoint read of one site tensor (App. B.2 continues a propagation from the full augmented MPS):
