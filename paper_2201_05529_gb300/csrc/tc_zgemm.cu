@@ -92,6 +92,25 @@ __global__ void k_zg_rowexp(const ZGemmItem* items, int n_items, int which) {
   const PackCap cp = zcap(it, which);
   int* ex = (int*)((which == 0 ? it.TA : it.TB) + cp.exp_off);
   const int padded = cdiv(rows, tr) * tr;
+  const bool k_contiguous = which == 0 ? it.opA != ZOP_N : it.opB == ZOP_N;
+  if (k_contiguous) {
+    // a row's entries are contiguous in memory: one warp per row, its lanes striding K (the
+    // maximum does not depend on the order, so the exponent is the same as a sequential scan's)
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < padded; r += gridDim.x * wpb) {
+      double m = 0.0;
+      if (r < rows)
+        for (int k = lane; k < it.K; k += 32) {
+          const double2 v = op_elem(it, which, r, k);
+          m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) ex[r] = row_exponent(m);
+    }
+    return;
+  }
+  // consecutive rows are contiguous: one thread per row, consecutive threads on consecutive rows
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < padded; r += gridDim.x * blockDim.x) {
     double m = 0.0;
     if (r < rows)
@@ -368,7 +387,7 @@ bool g_zattr_done[ZMAX_DEV] = {};
 
 void launch_zgemm_pack_a(const ZGemmItem* items, int n_items, int m_cap_max, int* status, cudaStream_t st) {
   if (n_items <= 0) return;
-  const int bx_a = std::min(64, cdiv(std::max(1, m_cap_max), 128));
+  const int bx_a = std::min(1024, cdiv(std::max(1, m_cap_max), 4));     // four rows per block when a warp takes a row
   k_zg_rowexp<<<dim3(bx_a, n_items), 128, 0, st>>>(items, n_items, -1);
   k_zg_pack<<<dim3(128, n_items), 256, 0, st>>>(items, n_items, -1, status);
 }
@@ -376,7 +395,8 @@ void launch_zgemm_pack_a(const ZGemmItem* items, int n_items, int m_cap_max, int
 void launch_zgemm(const ZGemmItem* items, int n_items, int tile_cap, int m_cap_max, int n_cap_max, int* status,
                   cudaStream_t st) {
   if (n_items <= 0) return;
-  const int bx_a = std::min(64, cdiv(std::max(1, m_cap_max), 128)), bx_b = std::min(64, cdiv(std::max(1, n_cap_max), 128));
+  // four rows per block when a warp takes a row (rows contiguous in K), else 128
+  const int bx_a = std::min(1024, cdiv(std::max(1, m_cap_max), 4)), bx_b = std::min(1024, cdiv(std::max(1, n_cap_max), 4));
   k_zg_rowexp<<<dim3(bx_a, n_items), 128, 0, st>>>(items, n_items, 0);
   k_zg_rowexp<<<dim3(bx_b, n_items), 128, 0, st>>>(items, n_items, 1);
   k_zg_pack<<<dim3(128, n_items), 256, 0, st>>>(items, n_items, 0, status);
