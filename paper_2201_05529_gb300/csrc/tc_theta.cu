@@ -450,8 +450,9 @@ void launch_mode(const Tables& T, const BondWork* work, int n_work, int tile_cap
   constexpr int KSTEP = Geo<BF16>::KSTEP;
   const int gx = 64;
   if (SLICE) {
+    // one thread per row: A has r_L <= 512 rows, B' up to 4 n_D = 8192 (the gate-folded rows)
     k_tc_rowexp<<<dim3(4, n_work), 128, 0, st>>>(T, work, n_work, 0, KSTEP, NS);
-    k_tc_rowexp<<<dim3(16, n_work), 128, 0, st>>>(T, work, n_work, 1, KSTEP, NS);
+    k_tc_rowexp<<<dim3(64, n_work), 128, 0, st>>>(T, work, n_work, 1, KSTEP, NS);
   }
   k_tc_pack<BF16, NS, SLICE><<<dim3(gx, n_work), 256, 0, st>>>(T, work, n_work, 0);
   k_tc_pack<BF16, NS, SLICE><<<dim3(4 * gx, n_work), 256, 0, st>>>(T, work, n_work, 1);
